@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Throughput of the even-odd Wilson matrix on GB300.
+
+One step = M_eo^dag (M_eo psi): both a1-a7 rows of the hot path (neighbour
+indexing, projection, link multiply, reconstruction, the two hops of Eq. 4 with
+the diagonal term, and the adjoint), i.e. the normal-operator application a
+CG iteration on M_eo^dag M_eo performs. Workload: 32^3 x 64 periodic lattice,
+kappa = 0.13, links exp(i 0.4 H) with H random traceless Hermitian (seed 0),
+Gaussian even source (seed 0), FP32 storage and arithmetic, 18-real links.
+GFlop/s counts 1344 flop per site per M_eo (1320 per hopping site plus the
+kappa^2 scale and the subtraction).
+
+``python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]``
+prints one JSON line on rank 0. Under torchrun each rank runs an independent
+replica (the operator has no data-path exchange on one lattice per GPU).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "M_eo GFlop/s & HBM-roofline %, FP32 vs 16-bit; solve time to 1e-10 vs FP64"
+DIMS = (32, 32, 32, 64)
+KAPPA = 0.13
+EPS = 0.4
+FLOP_PER_SITE = 1344  # per M_eo per lattice site
+WORKLOAD = "M_eo^dag M_eo, 32^3x64, FP32, 18-real links, kappa=0.13, exp(i*0.4*H) links"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", default="f32")
+    ap.add_argument("--linkfmt", type=int, default=18)
+    ap.add_argument("--no-variants", action="store_true", help="skip the other precisions")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def fields(seed=0):
+    import gen
+
+    U = gen.gauge_field(DIMS, "smooth", seed=seed, eps=EPS)
+    psi = gen.gaussian_spinor(DIMS, seed=seed)[0]
+    return U, psi
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2303_08609_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic(label):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel source
+    it was taken from is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(label)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# algorithmic bytes per launch of each hopping-kernel kind, per lattice site V
+# (V/2 output sites): input spinors once + all 4V links once + output once,
+# + the axpy addend for the second hop.
+def algo_bytes_per_site(label):
+    if label.startswith("hop_f32"):
+        sp, lk = 96, (48 if "_l12" in label else 72)
+    elif label.startswith("hop_f64"):
+        sp, lk = 192, (96 if "_l12" in label else 144)
+    elif label.startswith("hop_to16"):
+        lk = 24 if "_l12" in label else 36
+        return (96 + 52) / 2 + 4 * lk
+    elif label.startswith("hop_from16"):
+        lk = 24 if "_l12" in label else 36
+        return (52 + 96 + 96) / 2 + 4 * lk
+    else:
+        return None
+    n_sp = 3 if "_axpy" in label else 2
+    return n_sp * sp / 2 + 4 * lk
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2303_08609_gb300 as weo
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    U, psi = fields()
+    V = int(np.prod(DIMS))
+    vh = V // 2
+    x_host = np.ascontiguousarray(np.moveaxis(psi, 0, -1)).astype(np.complex64)
+    x = torch.from_numpy(x_host).to(dev)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    op = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec,
+                      linkfmt=args.linkfmt)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        weo.wilson_eo_apply(op.handle, y, x, 1, stream)
+        weo.wilson_eo_apply_dag(op.handle, z, y, 1, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device events on the launching stream
+    weo.wilson_eo_profile(op.handle, True)
+    weo.wilson_eo_profile_read(op.handle, reset=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    prof = weo.wilson_eo_profile_read(op.handle, reset=True)
+    weo.wilson_eo_profile(op.handle, False)
+    ms_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    flops_step = 2 * FLOP_PER_SITE * V
+    value = world * flops_step / (ms_step * 1e-3) / 1e9
+    launches = int(sum(c for _, c in prof.values()))
+
+    # ---- roofline of the dominant kernel
+    label, (kms, kcnt) = max(prof.items(), key=lambda kv: kv[1][0])
+    avg_ms = kms / kcnt
+    per_site = algo_bytes_per_site(label)
+    algo = per_site * V
+    peak, peak_kind = measured_peaks()
+    achieved = algo / (avg_ms * 1e-3) / 1e9
+    traffic = stored_traffic(label)
+    roofline = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1),
+                "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": int(algo), "avg_launch_ms": round(avg_ms, 5),
+                "kernel_share": {k: round(v[0] / sum(w[0] for w in prof.values()), 4)
+                                 for k, v in sorted(prof.items())}}
+
+    # ---- sampled parity of this run's output (M_eo^dag M_eo at 64 sites)
+    check = None
+    if rank == 0:
+        try:
+            import oracle
+
+            sites = np.sort(np.random.default_rng(7).choice(vh, 64, replace=False))
+            got_y = np.moveaxis(y[:, :, torch.from_numpy(sites).to(dev)].cpu().numpy(), -1, 0)
+            want_y = oracle.meo_sites(U, KAPPA, psi, DIMS, sites)
+            check = {"meo_rel_l2_64_sites": float(np.linalg.norm(got_y - want_y)
+                                                  / np.linalg.norm(want_y))}
+        except Exception as exc:  # pragma: no cover
+            check = {"error": repr(exc)}
+
+    # ---- end to end: host (pinned) input -> M_eo -> M_eo^dag -> host output
+    xh = torch.from_numpy(x_host).pin_memory()
+    zh = torch.empty_like(xh).pin_memory()
+    nb = xh.numel() * xh.element_size()
+    for _ in range(2):
+        weo.wilson_eo_apply(op.handle, y, xh, 1, stream)
+        weo.wilson_eo_apply_dag(op.handle, zh, y, 1, stream)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    ke = max(5, args.steps // 2)
+    for _ in range(ke):
+        weo.wilson_eo_apply(op.handle, y, xh, 1, stream)
+        weo.wilson_eo_apply_dag(op.handle, zh, y, 1, stream)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / ke
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(world * flops_step / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GFlop/s",
+           "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+    # ---- other storage formats (same workload, M_eo^dag M_eo per step)
+    variants = {}
+    if not args.no_variants:
+        Ud = torch.from_numpy(U).to(dev)
+        for prec, fmt in (("f32", 12), ("f16", 18), ("f16", 12), ("bf16", 12), ("f64", 18)):
+            if (prec, fmt) == (args.prec, args.linkfmt):
+                continue
+            o2 = weo.WilsonEO(DIMS, KAPPA, Ud, prec=prec, linkfmt=fmt)
+            xv = x.to(torch.complex128) if prec == "f64" else x
+            yv, zv = torch.empty_like(xv), torch.empty_like(xv)
+            for _ in range(3):
+                weo.wilson_eo_apply(o2.handle, yv, xv, 1, stream)
+                weo.wilson_eo_apply_dag(o2.handle, zv, yv, 1, stream)
+            torch.cuda.synchronize()
+            n = 10 if prec == "f64" else 30
+            weo.wilson_eo_profile(o2.handle, True)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(n):
+                weo.wilson_eo_apply(o2.handle, yv, xv, 1, stream)
+                weo.wilson_eo_apply_dag(o2.handle, zv, yv, 1, stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            vms = a0.elapsed_time(a1) / n
+            vp = weo.wilson_eo_profile_read(o2.handle, reset=True)
+            lab, (km, kc) = max(vp.items(), key=lambda kv: kv[1][0])
+            ab = algo_bytes_per_site(lab)
+            ent = {"gflops": round(flops_step / (vms * 1e-3) / 1e9, 1),
+                   "ms_per_step": round(vms, 4), "dominant_kernel": lab,
+                   "kernel_gbs": round(ab * V / (km / kc * 1e-3) / 1e9, 1) if ab else None}
+            yo = np.moveaxis(yv[:, :, torch.from_numpy(sites).to(dev)].cpu().numpy(), -1, 0) \
+                if rank == 0 and check and "error" not in check else None
+            if yo is not None:
+                ent["meo_rel_l2_64_sites"] = float(np.linalg.norm(yo - want_y)
+                                                   / np.linalg.norm(want_y))
+            variants[f"{prec}_l{fmt}"] = ent
+            o2.close()
+            del xv, yv, zv
+        del Ud
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(U, psi)
+
+    if rank == 0:
+        import oracle  # noqa: F401  (only for the baseline / check above)
+
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "f64": "f64", "f16": "f16-storage/f32",
+                      "bf16": "bf16-storage/f32"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA,
+                       "links": f"exp(i*{EPS}*H), {args.linkfmt}-real", "prec": args.prec,
+                       "flop_per_site_per_meo": FLOP_PER_SITE,
+                       "l2": "inputs larger than L2 (604 MB of links per hop pass)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "check": check, "variants": variants,
+        }
+        print(json.dumps(out), flush=True)
+    op.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def cpu_baseline(U, psi, reps=1):
+    """The FP64 oracle (OpenMP over all host cores) on the full workload step."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    V = int(np.prod(DIMS))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        yv = oracle.meo(U, KAPPA, psi, DIMS)
+        oracle.meo_dag(U, KAPPA, yv, DIMS)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": round(2 * FLOP_PER_SITE * V / dt / 1e9, 3), "unit": "GFlop/s",
+            "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"{reps} full step(s) of the workload (M_eo then M_eo^dag, FP64, "
+                      f"32^3x64), {dt:.2f} s each"}
+
+
+def run_reference(args, rank, world, local):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+
+    U, psi = fields()
+    V = int(np.prod(DIMS))
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    for _ in range(min(1, args.warmup)):
+        yv = oracle.meo(U, KAPPA, psi, DIMS)
+        oracle.meo_dag(U, KAPPA, yv, DIMS)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        yv = oracle.meo(U, KAPPA, psi, DIMS)
+        oracle.meo_dag(U, KAPPA, yv, DIMS)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2 * FLOP_PER_SITE * V / dt / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GFlop/s",
+           "n_gpus": world, "steps": args.steps, "warmup": min(1, args.warmup),
+           "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA},
+           "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s", "cores": threads,
+                            "kind": "oracle",
+                            "sample": "full workload step (M_eo then M_eo^dag, FP64, 32^3x64)"},
+           "e2e": {"value": round(value, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,155 @@
+/*
+ * wilson_eo.h -- C ABI of libwilson_eo.so, the even-odd preconditioned Wilson
+ * fermion matrix on one GB300 GPU (sm_103a).
+ *
+ * The operator (Kanamori, Nitadori, Matsufuru, arXiv:2303.08609):
+ *
+ *   D_W(x,y) = delta_{x,y} - kappa sum_mu [ (1 - gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                                        + (1 + gamma_mu) U_mu^dag(x-mu) delta_{x-mu,y} ]
+ *                                                         (Sec. 2, Eq. 1 and its footnote)
+ *   H_eo, H_oe : the hopping sum of Eq. 1 without -kappa, restricted to
+ *                odd->even and even->odd sites, so D_eo = -kappa H_eo, D_oe = -kappa H_oe
+ *   M_eo       = 1 - D_ee^-1 D_eo D_oo^-1 D_oe = 1 - kappa^2 H_eo H_oe
+ *                (Sec. 2, Eq. 4; D_ee = D_oo = 1 for the Wilson matrix)
+ *
+ * Conventions fixed by this library where the paper leaves them open:
+ *   - lattice: periodic in all four directions; every extent even and >= 2;
+ *     dims[] = {Lx, Ly, Lz, Lt}; V = Lx Ly Lz Lt;
+ *   - parity: a site (x,y,z,t) is even when x+y+z+t is even (Sec. 3.3);
+ *     the V/2 sites of one parity are numbered by i = lex/2 with
+ *     lex = ((t Lz + z) Ly + y) Lx + x (compaction in x, Sec. 3.3, Fig. 4);
+ *   - gamma basis: Euclidean chiral, gamma_k = [[0, -i sigma_k], [i sigma_k, 0]]
+ *     for k = x,y,z and gamma_t = [[0, 1], [1, 0]]; gamma_5 = diag(1,1,-1,-1);
+ *   - projector signs as in Eq. 1: (1 - gamma_mu) on the forward neighbour.
+ *
+ * Canonical external layouts (complex numbers interleaved re, im):
+ *   gauge   U[mu][lex][a][b]         mu = 0..3 (x,y,z,t), 4*V links of 3x3,
+ *                                    complex128 (gauge_is_f64 = 1) or complex64
+ *   spinor  psi[rhs][spin][colour][i] one parity, i = 0..V/2-1 fastest
+ *                                    (planar: each of the 12 spin-colour
+ *                                    components is a contiguous array of V/2
+ *                                    sites), complex128 for WEO_F64 handles and
+ *                                    complex64 for WEO_F32 / WEO_F16 / WEO_BF16
+ *   force   F[mu][lex][a][b]         like the gauge field, in the spinor dtype
+ *
+ * Pointers: every array argument may be device memory (cudaMalloc / torch) or
+ * host memory (pageable or pinned). Host arrays are staged through buffers the
+ * handle owns; a call with any host array blocks until its results are in host
+ * memory. Calls on device arrays are asynchronous on `stream` (a cudaStream_t,
+ * NULL = the legacy default stream) unless stated otherwise.
+ *
+ * Ownership: the caller owns every array it passes. The handle owns its packed
+ * gauge copies, its intermediate odd-site fields, solver workspaces, staging
+ * buffers and tuning state, and frees them in wilson_eo_destroy. A handle may be
+ * used from one host thread at a time, and its calls must be ordered on the
+ * device (one stream, or streams synchronised by the caller), because calls
+ * share the handle's intermediate buffers.
+ *
+ * Errors: every int-returning call returns WEO_OK (0) or a negative weo_status.
+ * No call aborts, exits, throws across the ABI or traps on the device.
+ * wilson_eo_last_error() describes the most recent failure of the calling thread.
+ */
+#ifndef WILSON_EO_H
+#define WILSON_EO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wilson_eo_s *wilson_eo_t;
+
+typedef enum {
+    WEO_OK = 0,
+    WEO_ERR_ARG = -1,           /* null pointer, nrhs < 1, bad enum, bad tolerance ... */
+    WEO_ERR_DIMS = -2,          /* an extent odd or < 2, or a volume too large */
+    WEO_ERR_UNSUPPORTED = -3,   /* combination not provided (e.g. batch of mixed precisions) */
+    WEO_ERR_CUDA = -4,          /* a CUDA runtime call or kernel launch failed */
+    WEO_ERR_NOT_CONVERGED = -5, /* solver hit maxiter; outputs hold the best iterate */
+    WEO_ERR_NONFINITE = -6,     /* NaN or Inf met in a solver reduction */
+    WEO_ERR_TIMEOUT = -7,       /* a bounded device-side wait gave up */
+    WEO_ERR_OOM = -8            /* device or host allocation failed */
+} weo_status;
+
+/* Storage precision of the Dirac operator inside a handle. WEO_F16 / WEO_BF16
+ * store spinors as 16-bit values scaled by a per-site FP32 norm (the maximum
+ * modulus of the site's 24 reals) and links as plain 16-bit values; all
+ * arithmetic is FP32. */
+typedef enum { WEO_F64 = 0, WEO_F32 = 1, WEO_F16 = 2, WEO_BF16 = 3 } weo_prec;
+
+/* Link storage: all 18 reals, or rows 0 and 1 only (12 reals) with row 2 rebuilt
+ * in registers as conj(row0 x row1), exact for SU(3) up to rounding. */
+typedef enum { WEO_LINK18 = 0, WEO_LINK12 = 1 } weo_linkfmt;
+
+/* Create a handle for one lattice.
+ *   out      receives the handle (set to NULL on failure)
+ *   dims     {Lx, Ly, Lz, Lt}, each even and >= 2 (WEO_ERR_DIMS otherwise);
+ *            V/2 must stay below 2^31
+ *   kappa    hopping parameter of Eq. 1 (kappa = 1/(8 + 2m))
+ *   prec     weo_prec; linkfmt weo_linkfmt
+ *   gauge    canonical gauge field (4*V*9 complex), copied and packed; the caller
+ *            may free it when the call returns
+ * Blocks until the packed copy is complete. */
+int wilson_eo_create(wilson_eo_t *out, const int dims[4], double kappa, int prec, int linkfmt,
+                     const void *gauge, int gauge_is_f64, void *stream);
+
+/* Replace the gauge field (same layout and rules as in create). */
+int wilson_eo_set_gauge(wilson_eo_t h, const void *gauge, int gauge_is_f64, void *stream);
+
+/* Change kappa (host-side state only; takes effect for later calls). */
+int wilson_eo_set_kappa(wilson_eo_t h, double kappa);
+
+/* Query: dims (int[4]), V/2, precision, link format, kappa, and the bytes the
+ * handle holds on the device. Any output pointer may be NULL. */
+int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *prec,
+                   int *linkfmt, double *kappa, size_t *device_bytes);
+
+/* out_e = M_eo in_e = in_e - kappa^2 H_eo H_oe in_e   (Eq. 4)
+ * in_e, out_e: nrhs canonical even spinors. out_e must not alias in_e.
+ * nrhs >= 1; right-hand sides share the links, which are read once per site
+ * for a block of right-hand sides. */
+int wilson_eo_apply(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, void *stream);
+
+/* out_e = M_eo^dag in_e = gamma_5 M_eo gamma_5 in_e, the adjoint of Eq. 4
+ * (gamma_5-hermiticity of Eq. 1). Same arguments and rules as apply. */
+int wilson_eo_apply_dag(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, void *stream);
+
+/* One hopping term of Eq. 1 (no kappa): out = H_{po,1-po} in, onto the sites of
+ * parity out_parity (0: H_eo, odd -> even; 1: H_oe, even -> odd), dag != 0 for
+ * its adjoint. in and out are canonical single-parity spinors. Not provided for
+ * 16-bit handles (WEO_ERR_UNSUPPORTED): their intermediates are internal. */
+int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void *in, int nrhs,
+                  void *stream);
+
+/* Launch configuration of the hopping kernels for the handle's precision:
+ * threads per block (32..256, a multiple of 32) and right-hand sides per
+ * thread (1, 2 or 4; values other than 1 apply to FP32 handles only, where the
+ * links loaded for a site are shared by that many right-hand sides).
+ * wilson_eo_tune (when present) sets these from measurements. */
+int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved);
+
+/* Per-kernel timing. With profiling on, every kernel the handle launches is
+ * bracketed by two CUDA events on its stream (a few microseconds of host time
+ * per launch). wilson_eo_profile_read waits for the recorded events and reports
+ * up to max_kernels entries: kernel label (names + k*name_len, NUL-terminated),
+ * summed device milliseconds and launch count; reset != 0 clears the totals. */
+int wilson_eo_profile(wilson_eo_t h, int enable);
+int wilson_eo_profile_read(wilson_eo_t h, int max_kernels, char *names, int name_len,
+                           double *total_ms, long long *launches, int *n_kernels, int reset);
+
+/* Release everything the handle owns (synchronises the device first).
+ * NULL is accepted. */
+void wilson_eo_destroy(wilson_eo_t h);
+
+/* Static description of a weo_status value. */
+const char *wilson_eo_strerror(int status);
+
+/* Message of the most recent failure in the calling thread ("" if none). */
+const char *wilson_eo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WILSON_EO_H */

@@ -1,0 +1,318 @@
+"""Even-odd Wilson fermion matrix on GB300 -- Python binding of ``libwilson_eo.so``.
+
+The C ABI (``include/wilson_eo.h``) is the product; this module only marshals
+arguments to it through ``ctypes``: torch tensors (CUDA or CPU) and numpy
+arrays are passed as raw pointers, torch's current CUDA stream is passed as the
+stream. Every step of the computation runs in the library's CUDA kernels. If
+the library is missing, every call raises: there is no CPU fallback.
+
+Function names match the C ABI (``wilson_eo_create``, ``wilson_eo_apply`` ...);
+:class:`WilsonEO` wraps a handle for convenience.
+
+Canonical layouts (see the header for details):
+
+* gauge ``(4, V, 3, 3)`` complex128 or complex64, sites lexicographic
+  ``((t*Lz+z)*Ly+y)*Lx+x``;
+* even/odd spinors, planar: ``(nrhs, 4, 3, V/2)`` complex128 (FP64 handles) or
+  complex64 (FP32 / FP16 / BF16 handles), site index ``lex // 2``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwilson_eo.so")
+
+WEO_OK = 0
+STATUS = {
+    0: "WEO_OK", -1: "WEO_ERR_ARG", -2: "WEO_ERR_DIMS", -3: "WEO_ERR_UNSUPPORTED",
+    -4: "WEO_ERR_CUDA", -5: "WEO_ERR_NOT_CONVERGED", -6: "WEO_ERR_NONFINITE",
+    -7: "WEO_ERR_TIMEOUT", -8: "WEO_ERR_OOM",
+}
+PREC = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+LINKFMT = {18: 0, 12: 1}
+
+_lib = None
+
+
+class WilsonEOError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_2303_08609_gb300.build` "
+            "(nvcc for sm_103a); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL, SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                       ctypes.c_size_t)
+    IP = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "wilson_eo_create": (I, [ctypes.POINTER(P), IP, D, I, I, P, I, P]),
+        "wilson_eo_set_gauge": (I, [P, P, I, P]),
+        "wilson_eo_set_kappa": (I, [P, D]),
+        "wilson_eo_info": (I, [P, IP, ctypes.POINTER(LL), IP, IP, ctypes.POINTER(D),
+                               ctypes.POINTER(SZ)]),
+        "wilson_eo_apply": (I, [P, P, P, I, P]),
+        "wilson_eo_apply_dag": (I, [P, P, P, I, P]),
+        "wilson_eo_hop": (I, [P, I, I, P, P, I, P]),
+        "wilson_eo_set_launch": (I, [P, I, I, I]),
+        "wilson_eo_profile": (I, [P, I]),
+        "wilson_eo_profile_read": (I, [P, I, ctypes.c_char_p, I, ctypes.POINTER(D),
+                                       ctypes.POINTER(LL), IP, I]),
+        "wilson_eo_destroy": (None, [P]),
+        "wilson_eo_strerror": (ctypes.c_char_p, [I]),
+        "wilson_eo_last_error": (ctypes.c_char_p, []),
+    }
+    optional = {
+        "wilson_eo_force": (I, [P, P, P, P, P]),
+        "wilson_eo_link_grad": (I, [P, P, P, P, P]),
+        "wilson_eo_solve": (I, [P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
+        "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                      ctypes.POINTER(P), I, P]),
+        "wilson_eo_tune": (I, [P, I, P]),
+        "wilson_eo_apply_fused": (I, [P, P, P, I, I, P]),
+        "wilson_eo_apply_fused_noalloc": (I, [P, P, P, I, P]),
+    }
+    for name, (res, args) in list(sig.items()) + list(optional.items()):
+        f = getattr(lib, name, None)
+        if f is None:
+            if name in sig:
+                raise RuntimeError(f"{LIB_PATH} does not export {name}")
+            continue
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def library():
+    """The loaded ``ctypes.CDLL`` (raises if the library was not built)."""
+    return _load()
+
+
+def _check(status: int, where: str):
+    if status != WEO_OK:
+        msg = _load().wilson_eo_last_error().decode(errors="replace")
+        raise WilsonEOError(status, where, msg)
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    raise TypeError(f"cannot pass {type(a)} to the C ABI")
+
+
+def _stream(stream):
+    """cudaStream_t of ``stream``: a torch.cuda.Stream, an int handle, or None
+    for torch's current stream (the legacy default stream without torch CUDA)."""
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------- C ABI, by name --
+
+
+def wilson_eo_create(dims, kappa, prec, linkfmt, gauge, gauge_is_f64=None, stream=None):
+    """Create a handle; ``prec`` in PREC names or ints, ``linkfmt`` 18/12 or 0/1."""
+    lib = _load()
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    f = {18: 0, 12: 1, 0: 0, 1: 1}[int(linkfmt)]
+    if gauge_is_f64 is None:
+        gauge_is_f64 = _is_f64(gauge)
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    h = ctypes.c_void_p()
+    _check(lib.wilson_eo_create(ctypes.byref(h), d, float(kappa), p, f, _ptr(gauge),
+                                int(bool(gauge_is_f64)), _stream(stream)), "wilson_eo_create")
+    return h
+
+
+def wilson_eo_set_gauge(h, gauge, gauge_is_f64=None, stream=None):
+    if gauge_is_f64 is None:
+        gauge_is_f64 = _is_f64(gauge)
+    _check(_load().wilson_eo_set_gauge(h, _ptr(gauge), int(bool(gauge_is_f64)), _stream(stream)),
+           "wilson_eo_set_gauge")
+
+
+def wilson_eo_set_kappa(h, kappa):
+    _check(_load().wilson_eo_set_kappa(h, float(kappa)), "wilson_eo_set_kappa")
+
+
+def wilson_eo_info(h):
+    d = (ctypes.c_int * 4)()
+    vh = ctypes.c_longlong()
+    p = ctypes.c_int()
+    f = ctypes.c_int()
+    k = ctypes.c_double()
+    b = ctypes.c_size_t()
+    _check(_load().wilson_eo_info(h, d, ctypes.byref(vh), ctypes.byref(p), ctypes.byref(f),
+                                  ctypes.byref(k), ctypes.byref(b)), "wilson_eo_info")
+    return {"dims": tuple(d), "half_volume": vh.value, "prec": p.value, "linkfmt": f.value,
+            "kappa": k.value, "device_bytes": b.value}
+
+
+def wilson_eo_apply(h, out_e, in_e, nrhs=1, stream=None):
+    _check(_load().wilson_eo_apply(h, _ptr(out_e), _ptr(in_e), int(nrhs), _stream(stream)),
+           "wilson_eo_apply")
+
+
+def wilson_eo_apply_dag(h, out_e, in_e, nrhs=1, stream=None):
+    _check(_load().wilson_eo_apply_dag(h, _ptr(out_e), _ptr(in_e), int(nrhs), _stream(stream)),
+           "wilson_eo_apply_dag")
+
+
+def wilson_eo_hop(h, out_parity, dag, out, inp, nrhs=1, stream=None):
+    _check(_load().wilson_eo_hop(h, int(out_parity), int(bool(dag)), _ptr(out), _ptr(inp),
+                                 int(nrhs), _stream(stream)), "wilson_eo_hop")
+
+
+def wilson_eo_set_launch(h, threads, rhs_block=1):
+    _check(_load().wilson_eo_set_launch(h, int(threads), int(rhs_block), 0), "wilson_eo_set_launch")
+
+
+def wilson_eo_profile(h, enable=True):
+    _check(_load().wilson_eo_profile(h, int(bool(enable))), "wilson_eo_profile")
+
+
+def wilson_eo_profile_read(h, reset=True, max_kernels=64):
+    """{kernel label: (total_ms, launches)} since the last reset."""
+    name_len = 96
+    names = ctypes.create_string_buffer(max_kernels * name_len)
+    ms = (ctypes.c_double * max_kernels)()
+    cnt = (ctypes.c_longlong * max_kernels)()
+    n = ctypes.c_int()
+    _check(_load().wilson_eo_profile_read(h, max_kernels, names, name_len, ms, cnt,
+                                          ctypes.byref(n), int(bool(reset))),
+           "wilson_eo_profile_read")
+    out = {}
+    for k in range(n.value):
+        label = names.raw[k * name_len:(k + 1) * name_len].split(b"\0", 1)[0].decode()
+        out[label] = (ms[k], cnt[k])
+    return out
+
+
+def wilson_eo_destroy(h):
+    if h:
+        _load().wilson_eo_destroy(h)
+
+
+def wilson_eo_strerror(status):
+    return _load().wilson_eo_strerror(int(status)).decode()
+
+
+def wilson_eo_last_error():
+    return _load().wilson_eo_last_error().decode(errors="replace")
+
+
+def _is_f64(a) -> bool:
+    dt = getattr(a, "dtype", None)
+    s = str(dt)
+    return "complex128" in s or "float64" in s
+
+
+# ------------------------------------------------------------ convenience --
+
+
+class WilsonEO:
+    """One lattice: gauge field, kappa, storage precision and link format.
+
+    ``gauge``: canonical ``(4, V, 3, 3)`` complex tensor/array (device or host).
+    Spinor arguments are planar ``(nrhs, 4, 3, V/2)`` or ``(4, 3, V/2)`` tensors.
+    """
+
+    def __init__(self, dims, kappa, gauge, prec="f32", linkfmt=18, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        self.prec = prec
+        self.linkfmt = linkfmt
+        self.vh = int(np.prod(self.dims)) // 2
+        self._h = wilson_eo_create(self.dims, kappa, prec, linkfmt, gauge, stream=stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            wilson_eo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def spinor_dtype(self):
+        import torch
+
+        return torch.complex128 if self.prec == "f64" else torch.complex64
+
+    def _nrhs(self, psi):
+        if tuple(psi.shape[-3:]) != (4, 3, self.vh):
+            raise ValueError(f"spinor shape must end in (4, 3, {self.vh}), got {tuple(psi.shape)}")
+        return 1 if psi.dim() == 3 else int(np.prod(psi.shape[:-3]))
+
+    def apply(self, psi, dag=False, out=None, stream=None):
+        """M_eo psi (or M_eo^dag psi)."""
+        import torch
+
+        nrhs = self._nrhs(psi)
+        out = torch.empty_like(psi) if out is None else out
+        (wilson_eo_apply_dag if dag else wilson_eo_apply)(self._h, out, psi, nrhs, stream)
+        return out
+
+    def hop(self, psi, out_parity, dag=False, out=None, stream=None):
+        import torch
+
+        nrhs = self._nrhs(psi)
+        out = torch.empty_like(psi) if out is None else out
+        wilson_eo_hop(self._h, out_parity, dag, out, psi, nrhs, stream)
+        return out
+
+    def set_gauge(self, gauge, stream=None):
+        wilson_eo_set_gauge(self._h, gauge, stream=stream)
+
+    def set_kappa(self, kappa):
+        self.kappa = float(kappa)
+        wilson_eo_set_kappa(self._h, kappa)
+
+    def info(self):
+        return wilson_eo_info(self._h)

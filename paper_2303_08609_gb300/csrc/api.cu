@@ -1,0 +1,381 @@
+// C ABI of libwilson_eo.so: handle life cycle, M_eo, M_eo^dag and single hops.
+#include <limits.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "weo_internal.h"
+
+namespace weo {
+
+const char *last_error_message();
+
+HopParams geom_params(const wilson_eo_s *h)
+{
+    HopParams p;
+    memset(&p, 0, sizeof(p));
+    p.lxh = h->dims[0] / 2;
+    p.ly = h->dims[1];
+    p.lz = h->dims[2];
+    p.lt = h->dims[3];
+    p.vh = (int)h->vh;
+    return p;
+}
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    int want = -1;
+    explicit DeviceGuard(int dev) : want(dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            return;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+static bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Input array: device pointers pass through, host arrays are copied into `buf`.
+static int stage_in(Buffer &buf, const void *p, size_t bytes, cudaStream_t s, const void **dev)
+{
+    if (is_device_pointer(p)) {
+        *dev = p;
+        return WEO_OK;
+    }
+    WEO_TRY(buf.ensure(bytes));
+    WEO_CUDA(cudaMemcpyAsync(buf.ptr, p, bytes, cudaMemcpyHostToDevice, s));
+    *dev = buf.ptr;
+    return WEO_OK;
+}
+
+// Output array: device pointers pass through, host arrays get a device buffer
+// whose contents finish_out copies back (blocking).
+static int stage_out(Buffer &buf, void *p, size_t bytes, void **dev, bool *host)
+{
+    *host = !is_device_pointer(p);
+    if (!*host) {
+        *dev = p;
+        return WEO_OK;
+    }
+    WEO_TRY(buf.ensure(bytes));
+    *dev = buf.ptr;
+    return WEO_OK;
+}
+
+static int finish_out(void *host_ptr, const void *dev, size_t bytes, bool host, cudaStream_t s)
+{
+    if (!host) return WEO_OK;
+    WEO_CUDA(cudaMemcpyAsync(host_ptr, dev, bytes, cudaMemcpyDeviceToHost, s));
+    WEO_CUDA(cudaStreamSynchronize(s));
+    return WEO_OK;
+}
+
+// bytes of one external (canonical) spinor of the handle
+static size_t ext_spinor_bytes(const wilson_eo_s *h)
+{
+    return (size_t)h->vh * (h->prec == WEO_F64 ? 192 : 96);
+}
+
+static int check_dims(const int *dims, long long *vh)
+{
+    if (!dims) return set_error(WEO_ERR_ARG, "dims is NULL");
+    long long v = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        if (dims[mu] < 2 || dims[mu] % 2)
+            return set_error(WEO_ERR_DIMS, "every lattice extent must be even and >= 2");
+        v *= dims[mu];
+        if (v > (long long)INT_MAX * 2) return set_error(WEO_ERR_DIMS, "volume too large");
+    }
+    *vh = v / 2;
+    return WEO_OK;
+}
+
+static int upload_gauge(wilson_eo_s *h, const void *gauge, int gauge_is_f64, cudaStream_t s)
+{
+    const size_t bytes = (size_t)(2 * h->vh) * 4 * 9 * (gauge_is_f64 ? 16 : 8);
+    WEO_TRY(h->canon_gauge.ensure(bytes));
+    const cudaMemcpyKind kind =
+        is_device_pointer(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    WEO_CUDA(cudaMemcpyAsync(h->canon_gauge.ptr, gauge, bytes, kind, s));
+    h->canon_is_f64 = gauge_is_f64 ? 1 : 0;
+    h->gauge_f64.valid = false;
+    h->gauge_lo.valid = false;
+    WEO_TRY(pack_gauge(h, h->gauge, h->prec, h->fmt, h->canon_gauge.ptr, h->canon_is_f64, s));
+    WEO_CUDA(cudaStreamSynchronize(s));
+    return WEO_OK;
+}
+
+int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
+               cudaStream_t s)
+{
+    int tok = -1;
+    if (h->prof) {
+        const char *kind = io == IO_TO16 ? "hop_to16" : io == IO_FROM16 ? "hop_from16" : "hop";
+        tok = prof_begin(h, kernel_label(kind, prec, fmt, dag, axpy).c_str(), s);
+    }
+    int st = launch_hop(prec, fmt, io, dag, axpy, p, h->cfg[prec], s);
+    prof_end(h, tok, s);
+    return st;
+}
+
+// M_eo (dag = false) or M_eo^dag on device pointers.
+int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s)
+{
+    HopParams p = geom_params(h);
+    p.nrhs = nrhs;
+    p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
+    p.gauge_pb = h->gauge.pb;
+    const long long ext = (long long)ext_spinor_bytes(h);
+    if (h->prec == WEO_F64 || h->prec == WEO_F32) {
+        WEO_TRY(h->tmp.ensure((size_t)ext * nrhs));
+        p.out_parity = 1;
+        p.in = in;
+        p.in_stride = ext;
+        p.out = h->tmp.ptr;
+        p.out_stride = ext;
+        WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, dag, false, p, s));
+        p.out_parity = 0;
+        p.in = h->tmp.ptr;
+        p.out = out;
+        p.x = in;
+        p.x_stride = ext;
+        p.a = -h->kappa * h->kappa;
+        return handle_hop(h, h->prec, h->fmt, IO_SAME, dag, true, p, s);
+    }
+    const long long s16 = h->vh * spinor_site_bytes(SK_H16);
+    WEO_TRY(h->tmp.ensure((size_t)s16 * nrhs));
+    p.out_parity = 1;
+    p.in = in;
+    p.in_stride = ext;
+    p.out = h->tmp.ptr;
+    p.out_stride = s16;
+    WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_TO16, dag, false, p, s));
+    p.out_parity = 0;
+    p.in = h->tmp.ptr;
+    p.in_stride = s16;
+    p.out = out;
+    p.out_stride = ext;
+    p.x = in;
+    p.x_stride = ext;
+    p.a = -h->kappa * h->kappa;
+    return handle_hop(h, h->prec, h->fmt, IO_FROM16, dag, true, p, s);
+}
+
+static int apply_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, bool dag,
+                        void *stream)
+{
+    if (!h || !out_e || !in_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+    if (nrhs < 1) return set_error(WEO_ERR_ARG, "nrhs must be >= 1");
+    if (out_e == in_e) return set_error(WEO_ERR_ARG, "out_e must not alias in_e");
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = ext_spinor_bytes(h) * (size_t)nrhs;
+    const void *in;
+    void *out;
+    bool out_host;
+    WEO_TRY(stage_in(h->stage_in, in_e, bytes, s, &in));
+    WEO_TRY(stage_out(h->stage_out, out_e, bytes, &out, &out_host));
+    WEO_TRY(meo_device(h, out, in, nrhs, dag, s));
+    if (!out_host && in != in_e) WEO_CUDA(cudaStreamSynchronize(s));
+    return finish_out(out_e, out, bytes, out_host, s);
+}
+
+}  // namespace weo
+
+using namespace weo;
+
+extern "C" {
+
+int wilson_eo_create(wilson_eo_t *out, const int dims[4], double kappa, int prec, int linkfmt,
+                     const void *gauge, int gauge_is_f64, void *stream)
+{
+    try {
+        if (!out) return set_error(WEO_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        long long vh;
+        WEO_TRY(check_dims(dims, &vh));
+        if (prec < WEO_F64 || prec > WEO_BF16) return set_error(WEO_ERR_ARG, "unknown precision");
+        if (linkfmt != WEO_LINK18 && linkfmt != WEO_LINK12)
+            return set_error(WEO_ERR_ARG, "unknown link format");
+        if (!gauge) return set_error(WEO_ERR_ARG, "gauge is NULL");
+        wilson_eo_s *h = new (std::nothrow) wilson_eo_s();
+        if (!h) return set_error(WEO_ERR_OOM, "host allocation failed");
+        for (int mu = 0; mu < 4; ++mu) h->dims[mu] = dims[mu];
+        h->vh = vh;
+        h->kappa = kappa;
+        h->prec = prec;
+        h->fmt = linkfmt;
+        if (cudaGetDevice(&h->device) != cudaSuccess) {
+            delete h;
+            return fail_cuda(cudaGetLastError(), "cudaGetDevice", __FILE__, __LINE__);
+        }
+        int st = upload_gauge(h, gauge, gauge_is_f64, static_cast<cudaStream_t>(stream));
+        if (st != WEO_OK) {
+            wilson_eo_destroy(h);
+            return st;
+        }
+        *out = h;
+        return WEO_OK;
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_create");
+    }
+}
+
+int wilson_eo_set_gauge(wilson_eo_t h, const void *gauge, int gauge_is_f64, void *stream)
+{
+    try {
+        if (!h || !gauge) return set_error(WEO_ERR_ARG, "NULL handle or gauge");
+        DeviceGuard g(h->device);
+        return upload_gauge(h, gauge, gauge_is_f64, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_set_gauge");
+    }
+}
+
+int wilson_eo_set_kappa(wilson_eo_t h, double kappa)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    h->kappa = kappa;
+    return WEO_OK;
+}
+
+int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved)
+{
+    (void)reserved;
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (threads < 32 || threads > 1024 || threads % 32)
+        return set_error(WEO_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
+    if (rhs_block != 1 && rhs_block != 2 && rhs_block != 4)
+        return set_error(WEO_ERR_ARG, "rhs_block must be 1, 2 or 4");
+    if (rhs_block != 1 && h->prec != WEO_F32)
+        return set_error(WEO_ERR_UNSUPPORTED, "rhs_block > 1 needs an FP32 handle");
+    if (threads > 256) return set_error(WEO_ERR_UNSUPPORTED, "hopping kernels are built for <= 256 threads");
+    h->cfg[h->prec].threads = threads;
+    h->cfg[h->prec].rhs_block = rhs_block;
+    return WEO_OK;
+}
+
+int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *prec,
+                   int *linkfmt, double *kappa, size_t *device_bytes)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (dims_out)
+        for (int mu = 0; mu < 4; ++mu) dims_out[mu] = h->dims[mu];
+    if (half_volume) *half_volume = h->vh;
+    if (prec) *prec = h->prec;
+    if (linkfmt) *linkfmt = h->fmt;
+    if (kappa) *kappa = h->kappa;
+    if (device_bytes)
+        *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
+                        h->canon_gauge.bytes + h->tmp.bytes + h->stage_in.bytes +
+                        h->stage_out.bytes + h->stage_aux.bytes;
+    return WEO_OK;
+}
+
+int wilson_eo_apply(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, void *stream)
+{
+    try {
+        return apply_common(h, out_e, in_e, nrhs, false, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply");
+    }
+}
+
+int wilson_eo_apply_dag(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, void *stream)
+{
+    try {
+        return apply_common(h, out_e, in_e, nrhs, true, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply_dag");
+    }
+}
+
+int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void *in, int nrhs,
+                  void *stream)
+{
+    try {
+        if (!h || !out || !in) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (nrhs < 1) return set_error(WEO_ERR_ARG, "nrhs must be >= 1");
+        if (out_parity != 0 && out_parity != 1) return set_error(WEO_ERR_ARG, "out_parity must be 0 or 1");
+        if (out == in) return set_error(WEO_ERR_ARG, "out must not alias in");
+        if (h->prec != WEO_F64 && h->prec != WEO_F32)
+            return set_error(WEO_ERR_UNSUPPORTED, "wilson_eo_hop needs an FP64 or FP32 handle");
+        DeviceGuard g(h->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t ext = ext_spinor_bytes(h);
+        const size_t bytes = ext * (size_t)nrhs;
+        const void *din;
+        void *dout;
+        bool out_host;
+        WEO_TRY(stage_in(h->stage_in, in, bytes, s, &din));
+        WEO_TRY(stage_out(h->stage_out, out, bytes, &dout, &out_host));
+        HopParams p = geom_params(h);
+        p.nrhs = nrhs;
+        p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
+        p.gauge_pb = h->gauge.pb;
+        p.out_parity = out_parity;
+        p.in = din;
+        p.in_stride = (long long)ext;
+        p.out = dout;
+        p.out_stride = (long long)ext;
+        WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, dag != 0, false, p, s));
+        if (!out_host && din != in) WEO_CUDA(cudaStreamSynchronize(s));
+        return finish_out(out, dout, bytes, out_host, s);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_hop");
+    }
+}
+
+void wilson_eo_destroy(wilson_eo_t h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    h->gauge.buf.release();
+    h->gauge_f64.buf.release();
+    h->gauge_lo.buf.release();
+    h->canon_gauge.release();
+    h->tmp.release();
+    h->stage_in.release();
+    h->stage_out.release();
+    h->stage_aux.release();
+    prof_destroy(h);
+    delete h;
+}
+
+const char *wilson_eo_strerror(int status)
+{
+    switch (status) {
+    case WEO_OK: return "success";
+    case WEO_ERR_ARG: return "invalid argument";
+    case WEO_ERR_DIMS: return "invalid lattice dimensions";
+    case WEO_ERR_UNSUPPORTED: return "unsupported combination";
+    case WEO_ERR_CUDA: return "CUDA error";
+    case WEO_ERR_NOT_CONVERGED: return "solver did not converge";
+    case WEO_ERR_NONFINITE: return "non-finite value in solver";
+    case WEO_ERR_TIMEOUT: return "bounded device wait timed out";
+    case WEO_ERR_OOM: return "out of memory";
+    default: return "unknown status";
+    }
+}
+
+const char *wilson_eo_last_error(void) { return last_error_message(); }
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// Hopping kernel of the even-odd Wilson matrix, one output site per thread.
+//
+// Computes, for every site x of parity `out_parity` (Eq. 1 without -kappa):
+//   (H psi)(x) = sum_mu [ (1 - s gamma_mu) U_mu(x) psi(x+mu) + (1 + s gamma_mu) U_mu^dag(x-mu) psi(x-mu) ]
+// with s = +1, or s = -1 for the adjoint (H^dag swaps the projectors, which is
+// the gamma_5-hermiticity of Eq. 1). Mode Axpy writes out = x + a * (H psi),
+// which with a = -kappa^2 completes M_eo = 1 - kappa^2 H_eo H_oe (Eq. 4).
+//
+// Per direction the 4-spinor is projected onto a 2-spinor (the structure of
+// (1 -+ gamma_mu) in the chiral basis), multiplied by the link, and the two
+// lower spin components are rebuilt from the upper ones (Sec. 2, Fig. 2).
+// Chiral basis: gamma_mu = [[0, A_mu], [A_mu^dag, 0]] with A_x = -i sigma_1,
+// A_y = -i sigma_2, A_z = -i sigma_3, A_t = 1. For the projector (1 - S gamma):
+//   h = psi_up - S A psi_dn ;  chi = W h ;  out_up += chi ; out_dn += -S A^dag chi.
+//
+// Neighbour indexing on the x-compacted parity arrays (Sec. 3.3-3.4): with
+// x = 2 xh + p and p = (y+z+t+out_parity) & 1, the x+1 neighbour has compact
+// index xh + p and the x-1 neighbour xh - (1-p), both periodic in Lx/2; the
+// other directions are plain strides Lx/2, Lx Ly/2, Lx Ly Lz/2 with wrap.
+// This index arithmetic replaces the SIMD select/permute shuffles the paper
+// needs for its x and y shifts (Figs. 5-6).
+#pragma once
+
+#include "weo_fields.cuh"
+
+namespace weo {
+
+struct HopParams {
+    int lxh, ly, lz, lt;   // Lx/2 and the other extents
+    int vh;                // V/2
+    int out_parity;
+    int nrhs;
+    const void *in;        // input spinor (opposite parity), rhs stride in bytes
+    long long in_stride;
+    void *out;             // output spinor (out_parity)
+    long long out_stride;
+    const void *x;         // axpy addend (out_parity), may be null in hop mode
+    long long x_stride;
+    const char *gauge;     // packed links: field (mu, parity) at gauge + (2 mu + parity) * gauge_pb
+    long long gauge_pb;
+    double a;              // axpy coefficient
+};
+
+// h = psi_up - S A_mu psi_dn for one colour
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const cx<R> p0, const cx<R> p1, const cx<R> p2,
+                                        const cx<R> p3, cx<R> &h0, cx<R> &h1)
+{
+    if (MU == 0) {  // A = -i sigma_1: A psi_dn = (-i p3, -i p2)
+        h0 = S > 0 ? cadd(p0, cmuli(p3)) : csub(p0, cmuli(p3));
+        h1 = S > 0 ? cadd(p1, cmuli(p2)) : csub(p1, cmuli(p2));
+    } else if (MU == 1) {  // A = -i sigma_2 = [[0,-1],[1,0]]: A psi_dn = (-p3, p2)
+        h0 = S > 0 ? cadd(p0, p3) : csub(p0, p3);
+        h1 = S > 0 ? csub(p1, p2) : cadd(p1, p2);
+    } else if (MU == 2) {  // A = -i sigma_3: A psi_dn = (-i p2, i p3)
+        h0 = S > 0 ? cadd(p0, cmuli(p2)) : csub(p0, cmuli(p2));
+        h1 = S > 0 ? csub(p1, cmuli(p3)) : cadd(p1, cmuli(p3));
+    } else {  // A = 1
+        h0 = S > 0 ? csub(p0, p2) : cadd(p0, p2);
+        h1 = S > 0 ? csub(p1, p3) : cadd(p1, p3);
+    }
+}
+
+// out_up += chi ; out_dn += -S A^dag chi, for one colour
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct(cx<R> &o0, cx<R> &o1, cx<R> &o2, cx<R> &o3,
+                                            const cx<R> c0, const cx<R> c1)
+{
+    o0 = cadd(o0, c0);
+    o1 = cadd(o1, c1);
+    if (MU == 0) {  // A^dag chi = (i c1, i c0)
+        o2 = S > 0 ? csub(o2, cmuli(c1)) : cadd(o2, cmuli(c1));
+        o3 = S > 0 ? csub(o3, cmuli(c0)) : cadd(o3, cmuli(c0));
+    } else if (MU == 1) {  // A^dag chi = (c1, -c0)
+        o2 = S > 0 ? csub(o2, c1) : cadd(o2, c1);
+        o3 = S > 0 ? cadd(o3, c0) : csub(o3, c0);
+    } else if (MU == 2) {  // A^dag chi = (i c0, -i c1)
+        o2 = S > 0 ? csub(o2, cmuli(c0)) : cadd(o2, cmuli(c0));
+        o3 = S > 0 ? cadd(o3, cmuli(c1)) : csub(o3, cmuli(c1));
+    } else {  // A^dag chi = (c0, c1)
+        o2 = S > 0 ? csub(o2, c0) : cadd(o2, c0);
+        o3 = S > 0 ? csub(o3, c1) : cadd(o3, c1);
+    }
+}
+
+// One hopping direction for R right-hand sides. FWD: link U_mu(x), projector
+// (1 - S0 gamma); backward: link U_mu(x-mu)^dag, projector (1 + S0 gamma).
+template <class SIn, class Lk, int MU, bool FWD, int S0, int R, typename T>
+__device__ __forceinline__ void hop_dir(cx<T> (&acc)[R][12], const HopParams &p, long long nb,
+                                        long long link_idx, int link_par, int rhs0)
+{
+    constexpr int S = FWD ? S0 : -S0;
+    cx<T> U[3][3];
+    Lk::load(p.gauge + (2 * MU + link_par) * p.gauge_pb, p.vh, link_idx, U);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (R > 1 && rhs0 + r >= p.nrhs) break;
+        cx<T> v[12];
+        SIn::load(static_cast<const char *>(p.in) + (rhs0 + r) * p.in_stride, p.vh, nb, v);
+        // spin-colour index k = 3*spin + colour
+        cx<T> h[2][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
+        cx<T> w[2][3];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                cx<T> z = {T(0), T(0)};
+#pragma unroll
+                for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[s][b], z) : cfmaconj(U[b][a], h[s][b], z);
+                w[s][a] = z;
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            reconstruct<MU, S>(acc[r][c], acc[r][3 + c], acc[r][6 + c], acc[r][9 + c], w[0][c], w[1][c]);
+    }
+}
+
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
+__global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
+{
+    using T = typename SOut::real;  // FP64 only when the output is FP64
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.vh) return;
+    const int rhs0 = blockIdx.y * R;
+    constexpr int S0 = Dag ? -1 : 1;
+
+    int rem = i;
+    const int xh = rem % p.lxh;
+    rem /= p.lxh;
+    const int y = rem % p.ly;
+    rem /= p.ly;
+    const int z = rem % p.lz;
+    const int t = rem / p.lz;
+    const int par = (y + z + t + p.out_parity) & 1;
+    const int in_par = p.out_parity ^ 1;
+
+    const int sy = p.lxh, sz = p.lxh * p.ly, st = p.lxh * p.ly * p.lz;
+    const int row = i - xh;
+    const int xp = par ? (xh + 1 == p.lxh ? 0 : xh + 1) : xh;
+    const int xm = par ? xh : (xh == 0 ? p.lxh - 1 : xh - 1);
+    const long long n_xp = row + xp, n_xm = row + xm;
+    const long long n_yp = i + (y + 1 == p.ly ? -(p.ly - 1) * sy : sy);
+    const long long n_ym = i + (y == 0 ? (p.ly - 1) * sy : -sy);
+    const long long n_zp = i + (z + 1 == p.lz ? -(p.lz - 1) * sz : sz);
+    const long long n_zm = i + (z == 0 ? (p.lz - 1) * sz : -sz);
+    const long long n_tp = i + (t + 1 == p.lt ? -(long long)(p.lt - 1) * st : st);
+    const long long n_tm = i + (t == 0 ? (long long)(p.lt - 1) * st : -st);
+
+    cx<T> acc[R][12];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[r][k] = {T(0), T(0)};
+
+    const int op = p.out_parity;
+    hop_dir<SIn, Lk, 0, true, S0, R>(acc, p, n_xp, i, op, rhs0);
+    hop_dir<SIn, Lk, 0, false, S0, R>(acc, p, n_xm, n_xm, in_par, rhs0);
+    hop_dir<SIn, Lk, 1, true, S0, R>(acc, p, n_yp, i, op, rhs0);
+    hop_dir<SIn, Lk, 1, false, S0, R>(acc, p, n_ym, n_ym, in_par, rhs0);
+    hop_dir<SIn, Lk, 2, true, S0, R>(acc, p, n_zp, i, op, rhs0);
+    hop_dir<SIn, Lk, 2, false, S0, R>(acc, p, n_zm, n_zm, in_par, rhs0);
+    hop_dir<SIn, Lk, 3, true, S0, R>(acc, p, n_tp, i, op, rhs0);
+    hop_dir<SIn, Lk, 3, false, S0, R>(acc, p, n_tm, n_tm, in_par, rhs0);
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (R > 1 && rhs0 + r >= p.nrhs) break;
+        if (Axpy) {
+            cx<T> xv[12];
+            SX::load(static_cast<const char *>(p.x) + (rhs0 + r) * p.x_stride, p.vh, i, xv);
+            const T a = T(p.a);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                acc[r][k].r = fma(a, acc[r][k].r, xv[k].r);
+                acc[r][k].i = fma(a, acc[r][k].i, xv[k].i);
+            }
+        }
+        SOut::store(static_cast<char *>(p.out) + (rhs0 + r) * p.out_stride, p.vh, i, acc[r]);
+    }
+}
+
+}  // namespace weo

@@ -1,0 +1,385 @@
+// Device-side storage formats of spinor and link fields, and complex helpers.
+//
+// Spinor formats (one parity, one right-hand side; site index i = lex/2):
+//   SpF64  [12][vh] double2   planar complex128 (the canonical FP64 layout)
+//   SpF32  [12][vh] float2    planar complex64  (the canonical FP32 layout)
+//   SpH16  [3][vh] uint4 + [vh] float   16-bit values scaled by a per-site norm:
+//          uint4 plane q holds spin-colour components 4q..4q+3 as half2 (re, im);
+//          norm[i] = max |real or imaginary part| over the site's 24 reals
+//   SpB16  like SpH16 with bfloat16 values
+// Link formats (one direction mu, one base-site parity; 3x3 complex per site):
+//   LkF64_18 [9][vh] double2            row-major U_ab
+//   LkF64_12 [6][vh] double2            rows 0, 1; row 2 = conj(row0 x row1)
+//   LkF32_18 [4][vh] float4 + [vh] float2
+//   LkF32_12 [3][vh] float4
+//   LkH16_18 [2][vh] uint4 + [vh] uint32 (half2 per complex)
+//   LkH16_12 [vh] uint4 + [vh] uint2
+//   LkB16_*  like LkH16_* with bfloat16
+// Every plane starts on a 16-byte boundary because vh = V/2 is a multiple of 8.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace weo {
+
+template <typename T>
+struct cx {
+    T r, i;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.r + b.r, a.i + b.i}; }
+template <typename T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return {a.r - b.r, a.i - b.i}; }
+// i * a
+template <typename T>
+__device__ __forceinline__ cx<T> cmuli(cx<T> a) { return {-a.i, a.r}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cneg(cx<T> a) { return {-a.r, -a.i}; }
+// acc + a * b
+template <typename T>
+__device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> acc)
+{
+    acc.r = fma(a.r, b.r, acc.r);
+    acc.r = fma(-a.i, b.i, acc.r);
+    acc.i = fma(a.r, b.i, acc.i);
+    acc.i = fma(a.i, b.r, acc.i);
+    return acc;
+}
+// acc + conj(a) * b
+template <typename T>
+__device__ __forceinline__ cx<T> cfmaconj(cx<T> a, cx<T> b, cx<T> acc)
+{
+    acc.r = fma(a.r, b.r, acc.r);
+    acc.r = fma(a.i, b.i, acc.r);
+    acc.i = fma(a.r, b.i, acc.i);
+    acc.i = fma(-a.i, b.r, acc.i);
+    return acc;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) { return cfma(a, b, cx<T>{0, 0}); }
+template <typename T>
+__device__ __forceinline__ cx<T> cconj(cx<T> a) { return {a.r, -a.i}; }
+template <typename T>
+__device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return {a.r * s, a.i * s}; }
+
+// ------------------------------------------------------------ loads/stores --
+// Spinor neighbour reads are re-used by up to eight output sites: plain cached
+// loads. Links are used once per pass: streaming loads (evict-first) so they do
+// not push the spinor working set out of L2.
+
+template <typename T>
+__device__ __forceinline__ T ld_keep(const T *p) { return __ldg(p); }
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------- spinors --
+
+struct SpF64 {
+    using real = double;
+    static constexpr int kBytesPerSite = 192;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            double2 d = ld_keep(p + k * vh + i);
+            v[k] = {R(d.x), R(d.y)};
+        }
+    }
+    template <typename R>
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<R> v[12])
+    {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k * vh + i] = make_double2(double(v[k].r), double(v[k].i));
+    }
+};
+
+struct SpF32 {
+    using real = float;
+    static constexpr int kBytesPerSite = 96;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const float2 *p = static_cast<const float2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float2 d = ld_keep(p + k * vh + i);
+            v[k] = {R(d.x), R(d.y)};
+        }
+    }
+    template <typename R>
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<R> v[12])
+    {
+        float2 *p = static_cast<float2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) p[k * vh + i] = make_float2(float(v[k].r), float(v[k].i));
+    }
+};
+
+struct H16Traits {
+    using scalar2 = __half2;
+    __device__ static __forceinline__ float2 to_f2(uint32_t u)
+    {
+        __half2 h = *reinterpret_cast<__half2 *>(&u);
+        return __half22float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float a, float b)
+    {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+};
+
+struct B16Traits {
+    using scalar2 = __nv_bfloat162;
+    __device__ static __forceinline__ float2 to_f2(uint32_t u)
+    {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+        return __bfloat1622float2(h);
+    }
+    __device__ static __forceinline__ uint32_t from_f2(float a, float b)
+    {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+};
+
+// 16-bit spinor with per-site FP32 norm; Tr = H16Traits or B16Traits.
+template <class Tr>
+struct Sp16 {
+    using real = float;
+    static constexpr int kBytesPerSite = 52;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float *nrm = reinterpret_cast<const float *>(p + 3 * vh);
+        const float n = ld_keep(nrm + i);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            uint4 w = ld_keep(p + q * vh + i);
+            float2 a = Tr::to_f2(w.x), b = Tr::to_f2(w.y), c = Tr::to_f2(w.z), d = Tr::to_f2(w.w);
+            v[4 * q + 0] = {R(a.x * n), R(a.y * n)};
+            v[4 * q + 1] = {R(b.x * n), R(b.y * n)};
+            v[4 * q + 2] = {R(c.x * n), R(c.y * n)};
+            v[4 * q + 3] = {R(d.x * n), R(d.y * n)};
+        }
+    }
+    template <typename R>
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<R> v[12])
+    {
+        uint4 *p = static_cast<uint4 *>(base);
+        float *nrm = reinterpret_cast<float *>(p + 3 * vh);
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(float(v[k].r)), fabsf(float(v[k].i))));
+        const float s = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            uint4 w;
+            w.x = Tr::from_f2(float(v[4 * q + 0].r) * s, float(v[4 * q + 0].i) * s);
+            w.y = Tr::from_f2(float(v[4 * q + 1].r) * s, float(v[4 * q + 1].i) * s);
+            w.z = Tr::from_f2(float(v[4 * q + 2].r) * s, float(v[4 * q + 2].i) * s);
+            w.w = Tr::from_f2(float(v[4 * q + 3].r) * s, float(v[4 * q + 3].i) * s);
+            p[q * vh + i] = w;
+        }
+        nrm[i] = m;
+    }
+};
+using SpH16 = Sp16<H16Traits>;
+using SpB16 = Sp16<B16Traits>;
+
+// ------------------------------------------------------------------ links --
+
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(cx<R> U[3][3])
+{
+    // row2 = conj(row0 x row1), exact for SU(3)
+    U[2][0] = cconj(csub(cmul(U[0][1], U[1][2]), cmul(U[0][2], U[1][1])));
+    U[2][1] = cconj(csub(cmul(U[0][2], U[1][0]), cmul(U[0][0], U[1][2])));
+    U[2][2] = cconj(csub(cmul(U[0][0], U[1][1]), cmul(U[0][1], U[1][0])));
+}
+
+struct LkF64_18 {
+    static constexpr int kBytesPerSite = 144;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double2 d = ld_stream(p + k * vh + i);
+            U[k / 3][k % 3] = {R(d.x), R(d.y)};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) p[k * vh + i] = make_double2(U[k / 3][k % 3].r, U[k / 3][k % 3].i);
+    }
+};
+
+struct LkF64_12 {
+    static constexpr int kBytesPerSite = 96;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            double2 d = ld_stream(p + k * vh + i);
+            U[k / 3][k % 3] = {R(d.x), R(d.y)};
+        }
+        reconstruct_row2(U);
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) p[k * vh + i] = make_double2(U[k / 3][k % 3].r, U[k / 3][k % 3].i);
+    }
+};
+
+struct LkF32_18 {
+    static constexpr int kBytesPerSite = 72;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+        float4 a = ld_stream(p + i), b = ld_stream(p + vh + i), c = ld_stream(p + 2 * vh + i),
+               d = ld_stream(p + 3 * vh + i);
+        float2 e = ld_stream(reinterpret_cast<const float2 *>(p + 4 * vh) + i);
+        U[0][0] = {R(a.x), R(a.y)};
+        U[0][1] = {R(a.z), R(a.w)};
+        U[0][2] = {R(b.x), R(b.y)};
+        U[1][0] = {R(b.z), R(b.w)};
+        U[1][1] = {R(c.x), R(c.y)};
+        U[1][2] = {R(c.z), R(c.w)};
+        U[2][0] = {R(d.x), R(d.y)};
+        U[2][1] = {R(d.z), R(d.w)};
+        U[2][2] = {R(e.x), R(e.y)};
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        float4 *p = static_cast<float4 *>(base);
+        p[i] = make_float4(U[0][0].r, U[0][0].i, U[0][1].r, U[0][1].i);
+        p[vh + i] = make_float4(U[0][2].r, U[0][2].i, U[1][0].r, U[1][0].i);
+        p[2 * vh + i] = make_float4(U[1][1].r, U[1][1].i, U[1][2].r, U[1][2].i);
+        p[3 * vh + i] = make_float4(U[2][0].r, U[2][0].i, U[2][1].r, U[2][1].i);
+        reinterpret_cast<float2 *>(p + 4 * vh)[i] = make_float2(U[2][2].r, U[2][2].i);
+    }
+};
+
+struct LkF32_12 {
+    static constexpr int kBytesPerSite = 48;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+        float4 a = ld_stream(p + i), b = ld_stream(p + vh + i), c = ld_stream(p + 2 * vh + i);
+        U[0][0] = {R(a.x), R(a.y)};
+        U[0][1] = {R(a.z), R(a.w)};
+        U[0][2] = {R(b.x), R(b.y)};
+        U[1][0] = {R(b.z), R(b.w)};
+        U[1][1] = {R(c.x), R(c.y)};
+        U[1][2] = {R(c.z), R(c.w)};
+        reconstruct_row2(U);
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        float4 *p = static_cast<float4 *>(base);
+        p[i] = make_float4(U[0][0].r, U[0][0].i, U[0][1].r, U[0][1].i);
+        p[vh + i] = make_float4(U[0][2].r, U[0][2].i, U[1][0].r, U[1][0].i);
+        p[2 * vh + i] = make_float4(U[1][1].r, U[1][1].i, U[1][2].r, U[1][2].i);
+    }
+};
+
+template <class Tr>
+struct Lk16_18 {
+    static constexpr int kBytesPerSite = 36;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        uint4 a = ld_stream(p + i), b = ld_stream(p + vh + i);
+        uint32_t e = ld_stream(reinterpret_cast<const unsigned int *>(p + 2 * vh) + i);
+        const uint32_t w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, e};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            float2 f = Tr::to_f2(w[k]);
+            U[k / 3][k % 3] = {R(f.x), R(f.y)};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        uint32_t w[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) w[k] = Tr::from_f2(float(U[k / 3][k % 3].r), float(U[k / 3][k % 3].i));
+        uint4 *p = static_cast<uint4 *>(base);
+        p[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        p[vh + i] = make_uint4(w[4], w[5], w[6], w[7]);
+        reinterpret_cast<unsigned int *>(p + 2 * vh)[i] = w[8];
+    }
+};
+
+template <class Tr>
+struct Lk16_12 {
+    static constexpr int kBytesPerSite = 24;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        uint4 a = ld_stream(p + i);
+        uint2 b = ld_stream_u2(reinterpret_cast<const uint2 *>(p + vh) + i);
+        const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float2 f = Tr::to_f2(w[k]);
+            U[k / 3][k % 3] = {R(f.x), R(f.y)};
+        }
+        reconstruct_row2(U);
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        uint32_t w[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] = Tr::from_f2(float(U[k / 3][k % 3].r), float(U[k / 3][k % 3].i));
+        uint4 *p = static_cast<uint4 *>(base);
+        p[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint2 *>(p + vh)[i] = make_uint2(w[4], w[5]);
+    }
+};
+
+using LkH16_18 = Lk16_18<H16Traits>;
+using LkH16_12 = Lk16_12<H16Traits>;
+using LkB16_18 = Lk16_18<B16Traits>;
+using LkB16_12 = Lk16_12<B16Traits>;
+
+}  // namespace weo

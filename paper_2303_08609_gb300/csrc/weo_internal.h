@@ -1,0 +1,126 @@
+// Internal declarations shared by the translation units of libwilson_eo.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <string>
+
+#include "../../include/wilson_eo.h"
+#include "weo_dslash.cuh"
+
+namespace weo {
+
+// ------------------------------------------------------------------ errors --
+int set_error(int status, const std::string &msg);
+int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+
+#define WEO_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::weo::fail_cuda(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define WEO_TRY(call)                \
+    do {                             \
+        int s_ = (call);             \
+        if (s_ != WEO_OK) return s_; \
+    } while (0)
+
+// ----------------------------------------------------------------- formats --
+// Spinor storage kinds inside the library.
+enum SpinorKind { SK_F64 = 0, SK_F32 = 1, SK_H16 = 2, SK_B16 = 3 };
+
+inline long long spinor_site_bytes(int kind)
+{
+    return kind == SK_F64 ? 192 : kind == SK_F32 ? 96 : 52;
+}
+inline long long link_site_bytes(int prec, int fmt)
+{
+    const bool c = fmt == WEO_LINK12;
+    switch (prec) {
+    case WEO_F64: return c ? 96 : 144;
+    case WEO_F32: return c ? 48 : 72;
+    default: return c ? 24 : 36;
+    }
+}
+
+// Device buffer that only grows.
+struct Buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t n);
+    void release();
+};
+
+// A packed gauge field in one precision / link format.
+struct PackedGauge {
+    Buffer buf;
+    int prec = -1;
+    int fmt = -1;
+    long long pb = 0;  // bytes of one (mu, parity) field
+    bool valid = false;
+};
+
+// Launch configuration chosen by the tuner (or defaults).
+struct LaunchCfg {
+    int threads = 128;
+    int rhs_block = 1;
+};
+
+struct Profiler;
+
+}  // namespace weo
+
+struct wilson_eo_s {
+    int dims[4];
+    long long vh;
+    double kappa;
+    int prec;
+    int fmt;
+    int device;
+    weo::PackedGauge gauge;      // in the handle's precision
+    weo::PackedGauge gauge_f64;  // solver: true residual (lazy)
+    weo::PackedGauge gauge_lo;   // solver: inner operator of an FP64 handle (lazy)
+    weo::Buffer canon_gauge;     // device copy of the canonical field (kept for lazy packs)
+    int canon_is_f64 = 1;
+    weo::Buffer tmp;             // odd-site intermediate
+    weo::Buffer stage_in, stage_out, stage_aux;
+    weo::LaunchCfg cfg[4];       // per spinor precision kind
+    weo::Profiler *prof = nullptr;
+};
+
+namespace weo {
+
+// geometry of a handle, without field pointers
+HopParams geom_params(const wilson_eo_s *h);
+
+// Launch the hopping kernel. io selects the storage combination:
+//   IO_SAME  : in, out and x all in the precision `prec` (F64 or F32)
+//   IO_TO16  : in FP32, out 16-bit (prec = WEO_F16 / WEO_BF16), hop mode only
+//   IO_FROM16: in 16-bit, out FP32, x FP32
+enum IoKind { IO_SAME = 0, IO_TO16 = 1, IO_FROM16 = 2 };
+int launch_hop(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
+               const LaunchCfg &cfg, cudaStream_t s);
+int launch_hop_f64(int fmt, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
+                   cudaStream_t s);
+int launch_hop_f32(int fmt, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
+                   cudaStream_t s);
+int launch_hop_16(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
+                  const LaunchCfg &cfg, cudaStream_t s);
+
+// Per-kernel event timing (prof.cu). prof_begin returns a token (-1 when off).
+int prof_begin(wilson_eo_s *h, const char *label, cudaStream_t s);
+void prof_end(wilson_eo_s *h, int token, cudaStream_t s);
+void prof_destroy(wilson_eo_s *h);
+std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axpy);
+
+// launch_hop for a handle, with its launch configuration and profiling
+int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
+               cudaStream_t s);
+
+// Pack a canonical gauge field (device memory) into `g` (allocates).
+int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *canon, int is_f64,
+               cudaStream_t s);
+
+}  // namespace weo

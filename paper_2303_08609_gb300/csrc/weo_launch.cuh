@@ -1,0 +1,29 @@
+// Template launcher for the hopping kernel: runtime (dag, axpy, rhs block) ->
+// compile-time instance. Included by one translation unit per precision.
+#pragma once
+
+#include "weo_internal.h"
+
+namespace weo {
+
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
+int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
+{
+    const int threads = cfg.threads;
+    dim3 grid((unsigned)((p.vh + threads - 1) / threads), (unsigned)((p.nrhs + R - 1) / R));
+    hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
+template <class SIn, class SOut, class SX, class Lk, int R>
+int launch_da(bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
+{
+    if (dag)
+        return axpy ? launch_instance<SIn, SOut, SX, Lk, true, true, R>(p, cfg, s)
+                    : launch_instance<SIn, SOut, SX, Lk, true, false, R>(p, cfg, s);
+    return axpy ? launch_instance<SIn, SOut, SX, Lk, false, true, R>(p, cfg, s)
+                : launch_instance<SIn, SOut, SX, Lk, false, false, R>(p, cfg, s);
+}
+
+}  // namespace weo

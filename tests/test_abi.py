@@ -1,0 +1,79 @@
+"""The C ABI library loads and exports every function ``include/*.h`` declares,
+and argument errors come back as status codes (no GPU needed for either)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(wilson_eo_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2303_08609_gb300 as weo
+
+    if not os.path.exists(weo.LIB_PATH):
+        from paper_2303_08609_gb300 import build
+
+        build.build()
+    return weo.library()
+
+
+def test_header_declares_the_core_entry_points():
+    names = declared_functions()
+    for n in ("wilson_eo_create", "wilson_eo_apply", "wilson_eo_apply_dag", "wilson_eo_destroy",
+              "wilson_eo_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_strerror_and_destroy_null(lib):
+    import paper_2303_08609_gb300 as weo
+
+    assert weo.wilson_eo_strerror(0) == "success"
+    assert "dimensions" in weo.wilson_eo_strerror(-2)
+    assert weo.wilson_eo_strerror(12345) == "unknown status"
+    weo.wilson_eo_destroy(None)  # no-op
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 4, 4), (4, 4, 4, 0), (4, 1, 4, 4), (4, 4, 5, 4)])
+def test_create_rejects_bad_dims_before_touching_the_device(lib, dims):
+    import paper_2303_08609_gb300 as weo
+
+    U = np.zeros((4, 1, 3, 3), dtype=np.complex128)
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_create(dims, 0.1, "f32", 18, U)
+    assert e.value.status == -2
+    assert "even" in weo.wilson_eo_last_error()
+
+
+def test_create_rejects_bad_enums_and_nulls(lib):
+    import paper_2303_08609_gb300 as weo
+
+    U = np.zeros((4, 16, 3, 3), dtype=np.complex128)
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(2, 2, 2, 2)
+    assert lib.wilson_eo_create(ctypes.byref(h), d, 0.1, 7, 0, U.ctypes.data, 1, None) == -1
+    assert lib.wilson_eo_create(ctypes.byref(h), d, 0.1, 1, 5, U.ctypes.data, 1, None) == -1
+    assert lib.wilson_eo_create(ctypes.byref(h), d, 0.1, 1, 0, None, 1, None) == -1
+    assert lib.wilson_eo_create(None, d, 0.1, 1, 0, U.ctypes.data, 1, None) == -1
+    assert lib.wilson_eo_apply(None, None, None, 1, None) == -1
+    assert lib.wilson_eo_info(None, None, None, None, None, None, None) == -1
+    assert weo.STATUS[-1] == "WEO_ERR_ARG"
