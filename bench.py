@@ -43,14 +43,21 @@ WORKLOAD = "M_eo^dag M_eo, 32^3x64, FP32, 18-real links, kappa=0.13, exp(i*0.4*H
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--linkfmt", type=int, default=18)
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    return ap.parse_args()
+    ap.add_argument("--dims", type=int, nargs=4, default=None,
+                    help="lattice extents (default 32 32 32 64, the benchmark workload)")
+    args = ap.parse_args()
+    if args.dims:
+        global DIMS, WORKLOAD
+        DIMS = tuple(args.dims)
+        WORKLOAD = WORKLOAD.replace("32^3x64", "x".join(map(str, DIMS)))
+    return args
 
 
 def dist_env():
@@ -68,12 +75,15 @@ def fields(seed=0):
     return U, psi
 
 
-def kernel_source_hash():
+# sources that define the FP32 hopping kernels whose DRAM traffic ncu measured
+HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "dslash_f32.cu")
+
+
+def kernel_source_hash(files=HOP_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2303_08609_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -279,7 +289,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    ke = max(5, args.steps // 2)
+    ke = max(5, min(200, args.steps // 4))
     for _ in range(ke):
         weo.wilson_eo_apply(op.handle, y, xh, 1, stream)
         weo.wilson_eo_apply_dag(op.handle, zh, y, 1, stream)
@@ -302,13 +312,14 @@ def run_ours(args, rank, world, local):
             if (prec, fmt) == (args.prec, args.linkfmt):
                 continue
             o2 = weo.WilsonEO(DIMS, KAPPA, Ud, prec=prec, linkfmt=fmt)
-            xv = x.to(torch.complex128) if prec == "f64" else x
+            xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev) \
+                if prec == "f64" else x
             yv, zv = torch.empty_like(xv), torch.empty_like(xv)
             for _ in range(3):
                 weo.wilson_eo_apply(o2.handle, yv, xv, 1, stream)
                 weo.wilson_eo_apply_dag(o2.handle, zv, yv, 1, stream)
             torch.cuda.synchronize()
-            n = 10 if prec == "f64" else 30
+            n = 20 if prec == "f64" else 200
             weo.wilson_eo_profile(o2.handle, True)
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)

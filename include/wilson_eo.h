@@ -122,6 +122,26 @@ int wilson_eo_apply_dag(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, 
 int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void *in, int nrhs,
                   void *stream);
 
+/* Euclidean gradient of the real function L = Re<g_e, M_eo phi_e> with respect
+ * to every link: grad[mu][lex][a][b] = dL/dRe U_mu(x)_ab + i dL/dIm U_mu(x)_ab
+ * (the convention torch uses for real losses of complex tensors), obtained by
+ * differentiating both hopping terms of Eq. 1 in M_eo = 1 - kappa^2 H_eo H_oe
+ * (Eq. 4). grad: canonical gauge layout in the spinor dtype (4*V*9 complex).
+ * With g_e = dLoss/d(M_eo phi_e) this is the link part of the backward pass.
+ * FP64 and FP32 handles only (WEO_ERR_UNSUPPORTED otherwise). */
+int wilson_eo_link_grad(wilson_eo_t h, void *grad, const void *g_e, const void *phi_e,
+                        void *stream);
+
+/* Pseudofermion force of S(U, phi) = |M_eo phi_e|^2 (the Schur-decomposed
+ * determinant of Sec. 2 evaluated with a noise vector phi): force[mu][lex] is
+ * the traceless anti-Hermitian 3x3 matrix F with dS/d eps = Re tr(X^dag F) for
+ * every traceless anti-Hermitian X under U_mu(x) -> exp(eps X) U_mu(x), i.e.
+ * F = TA(G U^dag) with G the link gradient for g_e = 2 M_eo phi_e and
+ * TA(W) = (W - W^dag)/2 - tr(W - W^dag)/6. If dS_dphi_e is not NULL it receives
+ * 2 M_eo^dag M_eo phi_e. Layouts as in wilson_eo_link_grad. FP64 / FP32 only. */
+int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi_e,
+                    void *stream);
+
 /* Launch configuration of the hopping kernels for the handle's precision:
  * threads per block (32..256, a multiple of 32) and right-hand sides per
  * thread (1, 2 or 4; values other than 1 apply to FP32 handles only, where the

@@ -222,6 +222,16 @@ def wilson_eo_profile_read(h, reset=True, max_kernels=64):
     return out
 
 
+def wilson_eo_link_grad(h, grad, g_e, phi_e, stream=None):
+    _check(_load().wilson_eo_link_grad(h, _ptr(grad), _ptr(g_e), _ptr(phi_e), _stream(stream)),
+           "wilson_eo_link_grad")
+
+
+def wilson_eo_force(h, force, dS_dphi_e, phi_e, stream=None):
+    _check(_load().wilson_eo_force(h, _ptr(force), _ptr(dS_dphi_e), _ptr(phi_e), _stream(stream)),
+           "wilson_eo_force")
+
+
 def wilson_eo_destroy(h):
     if h:
         _load().wilson_eo_destroy(h)
@@ -306,6 +316,26 @@ class WilsonEO:
         out = torch.empty_like(psi) if out is None else out
         wilson_eo_hop(self._h, out_parity, dag, out, psi, nrhs, stream)
         return out
+
+    def link_grad(self, g, phi, out=None, stream=None):
+        """Gradient of Re<g, M_eo phi> with respect to the links, (4, V, 3, 3)."""
+        import torch
+
+        V = 2 * self.vh
+        out = torch.empty((4, V, 3, 3), dtype=self.spinor_dtype(), device=phi.device) \
+            if out is None else out
+        wilson_eo_link_grad(self._h, out, g, phi, stream)
+        return out
+
+    def force(self, phi, want_dphi=False, stream=None):
+        """(F, dS/dphi or None) for S = |M_eo phi|^2."""
+        import torch
+
+        V = 2 * self.vh
+        F = torch.empty((4, V, 3, 3), dtype=self.spinor_dtype(), device=phi.device)
+        d = torch.empty_like(phi) if want_dphi else None
+        wilson_eo_force(self._h, F, d, phi, stream)
+        return F, d
 
     def set_gauge(self, gauge, stream=None):
         wilson_eo_set_gauge(self._h, gauge, stream=stream)

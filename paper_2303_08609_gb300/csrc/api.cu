@@ -284,7 +284,8 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
     if (kappa) *kappa = h->kappa;
     if (device_bytes)
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
-                        h->canon_gauge.bytes + h->tmp.bytes + h->stage_in.bytes +
+                        h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
+                        h->even1.bytes + h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
 }
@@ -343,6 +344,61 @@ int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void 
     }
 }
 
+int wilson_eo_link_grad(wilson_eo_t h, void *grad, const void *g_e, const void *phi_e,
+                        void *stream)
+{
+    try {
+        if (!h || !grad || !g_e || !phi_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (h->prec != WEO_F64 && h->prec != WEO_F32)
+            return set_error(WEO_ERR_UNSUPPORTED, "link gradient needs an FP64 or FP32 handle");
+        DeviceGuard dg(h->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t sb = ext_spinor_bytes(h);
+        const size_t gb = (size_t)(2 * h->vh) * 4 * 9 * (h->prec == WEO_F64 ? 16 : 8);
+        const void *g, *phi;
+        void *out;
+        bool out_host;
+        WEO_TRY(stage_in(h->stage_in, g_e, sb, s, &g));
+        WEO_TRY(stage_in(h->even1, phi_e, sb, s, &phi));
+        WEO_TRY(stage_out(h->stage_aux, grad, gb, &out, &out_host));
+        WEO_TRY(link_grad_device(h, out, g, phi, 0, s));
+        if (!out_host && (g != g_e || phi != phi_e)) WEO_CUDA(cudaStreamSynchronize(s));
+        return finish_out(grad, out, gb, out_host, s);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_link_grad");
+    }
+}
+
+int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi_e, void *stream)
+{
+    try {
+        if (!h || !force || !phi_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (h->prec != WEO_F64 && h->prec != WEO_F32)
+            return set_error(WEO_ERR_UNSUPPORTED, "force needs an FP64 or FP32 handle");
+        DeviceGuard dg(h->device);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t sb = ext_spinor_bytes(h);
+        const size_t gb = (size_t)(2 * h->vh) * 4 * 9 * (h->prec == WEO_F64 ? 16 : 8);
+        const void *phi;
+        void *out, *dphi = nullptr;
+        bool out_host, dphi_host = false;
+        WEO_TRY(stage_in(h->stage_in, phi_e, sb, s, &phi));
+        WEO_TRY(stage_out(h->stage_aux, force, gb, &out, &out_host));
+        if (dS_dphi_e) WEO_TRY(stage_out(h->stage_out, dS_dphi_e, sb, &dphi, &dphi_host));
+        WEO_TRY(h->even1.ensure(sb));
+        // g = dS/dchi = 2 M_eo phi
+        WEO_TRY(meo_device(h, h->even1.ptr, phi, 1, false, s));
+        WEO_TRY(scale_spinor(h, h->even1.ptr, 1, 2.0, s));
+        WEO_TRY(link_grad_device(h, out, h->even1.ptr, phi, 1, s));
+        if (dphi) WEO_TRY(meo_device(h, dphi, h->even1.ptr, 1, true, s));  // 2 M^dag M phi
+        if (!out_host && !dphi_host && phi != phi_e) WEO_CUDA(cudaStreamSynchronize(s));
+        if (dphi) WEO_TRY(finish_out(dS_dphi_e, dphi, sb, dphi_host, s));
+        return finish_out(force, out, gb, out_host, s);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_force");
+    }
+}
+
 void wilson_eo_destroy(wilson_eo_t h)
 {
     if (!h) return;
@@ -353,6 +409,9 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->gauge_lo.buf.release();
     h->canon_gauge.release();
     h->tmp.release();
+    h->tmp2.release();
+    h->tmp3.release();
+    h->even1.release();
     h->stage_in.release();
     h->stage_out.release();
     h->stage_aux.release();

@@ -84,7 +84,9 @@ struct wilson_eo_s {
     weo::PackedGauge gauge_lo;   // solver: inner operator of an FP64 handle (lazy)
     weo::Buffer canon_gauge;     // device copy of the canonical field (kept for lazy packs)
     int canon_is_f64 = 1;
-    weo::Buffer tmp;             // odd-site intermediate
+    weo::Buffer tmp;             // odd-site intermediate of M_eo
+    weo::Buffer tmp2, tmp3;      // odd-site fields of the link gradient
+    weo::Buffer even1;           // even-site field (force: 2 M_eo phi)
     weo::Buffer stage_in, stage_out, stage_aux;
     weo::LaunchCfg cfg[4];       // per spinor precision kind
     weo::Profiler *prof = nullptr;
@@ -118,6 +120,13 @@ std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axp
 // launch_hop for a handle, with its launch configuration and profiling
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
                cudaStream_t s);
+
+// M_eo / M_eo^dag on device arrays in the handle's external format (api.cu)
+int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s);
+// link gradient (force = 0) or force TA(G U^dag) (force = 1), force.cu
+int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, int force,
+                     cudaStream_t s);
+int scale_spinor(wilson_eo_s *h, void *v, int nrhs, double c, cudaStream_t s);
 
 // Pack a canonical gauge field (device memory) into `g` (allocates).
 int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *canon, int is_f64,
