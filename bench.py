@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--linkfmt", type=int, default=18)
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip multi-RHS, batch and force measurements")
+    ap.add_argument("--no-solve", action="store_true", help="skip the 48^3x96 solve comparison")
+    ap.add_argument("--only-solve", action="store_true", help="run only the solve comparison")
+    ap.add_argument("--solve-dims", type=int, nargs=4, default=[48, 48, 48, 96])
     ap.add_argument("--dims", type=int, nargs=4, default=None,
                     help="lattice extents (default 32 32 32 64, the benchmark workload)")
     args = ap.parse_args()
@@ -346,6 +351,9 @@ def run_ours(args, rank, world, local):
             del xv, yv, zv
         del Ud
 
+    extra = {} if args.no_extras else extras(U, psi, dev, stream)
+    solve = None if args.no_solve else solve_comparison(dev, tuple(args.solve_dims))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(U, psi)
@@ -367,6 +375,7 @@ def run_ours(args, rank, world, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "check": check, "variants": variants,
+            "extras": extra, "solve": solve,
         }
         print(json.dumps(out), flush=True)
     op.close()
@@ -374,6 +383,129 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+def timed(fn, n, stream):
+    import torch
+
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(n):
+        fn()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / n
+
+
+def extras(U, psi, dev, stream):
+    """Multi-RHS, mixed-lattice batch and force forward+backward on the GPU."""
+    import torch
+
+    import gen
+    import paper_2303_08609_gb300 as weo
+
+    V = int(np.prod(DIMS))
+    vh = V // 2
+    out = {}
+    Ud = torch.from_numpy(U).to(dev)
+    # 12 spin-colour point sources at one even site (FP32, links shared per site)
+    op = weo.WilsonEO(DIMS, KAPPA, Ud, prec="f32")
+    site = int(np.random.default_rng(3).integers(vh))
+    src = np.zeros((12, 4, 3, vh), dtype=np.complex64)
+    for s_ in range(4):
+        for c in range(3):
+            src[3 * s_ + c, s_, c, site] = 1.0
+    x = torch.from_numpy(src).to(dev)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    res = {}
+    for rb in (1, 2, 4):
+        weo.wilson_eo_set_launch(op.handle, 128, rb)
+        ms = timed(lambda: (weo.wilson_eo_apply(op.handle, y, x, 12, stream),
+                            weo.wilson_eo_apply_dag(op.handle, z, y, 12, stream)), 50, stream)
+        res[f"rhs_per_thread_{rb}"] = {"ms_per_step": round(ms, 4),
+                                       "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
+    t, rb, tms = weo.wilson_eo_tune(op.handle, 12, stream)
+    res["tuned"] = {"threads": t, "rhs_per_thread": rb, "ms_per_meo": round(tms, 4),
+                    "gflops": round(12 * FLOP_PER_SITE * V / (tms * 1e-3) / 1e9, 1)}
+    out["multi_rhs_12_point_sources_f32"] = res
+    del x, y, z
+    # force: chi = M phi forward, backward M^dag g + link gradient (FP32)
+    from paper_2303_08609_gb300.autograd import pseudofermion_action
+
+    Ur = Ud.to(torch.complex64)
+    opf = weo.WilsonEO(DIMS, KAPPA, Ur, prec="f32")
+    Ur.requires_grad_(True)
+    phi = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1)).astype(np.complex64)).to(dev)
+    phi.requires_grad_(True)
+
+    def fwd_bwd():
+        Ur.grad = None
+        phi.grad = None
+        S = pseudofermion_action(phi, Ur, opf, refresh=False)
+        S.backward()
+
+    ms = timed(fwd_bwd, 20, stream)
+    out["force_fwd_bwd_f32"] = {"ms_per_step": round(ms, 4),
+                                "note": "S=|M_eo phi|^2: M_eo forward, M_eo^dag + link gradient backward"}
+    opf.close()
+    op.close()
+    del Ud, Ur, phi
+    # one persistent launch over 16^4, 24^3x48, 32^3x64 (independent Haar links)
+    r = np.random.default_rng(5)
+    ops, xs, ys, sites = [], [], [], 0
+    for dims, seed in (((16, 16, 16, 16), 1), ((24, 24, 24, 48), 2), ((32, 32, 32, 64), 3)):
+        Uh = gen.gauge_field(dims, "haar", seed=seed)
+        ops.append(weo.WilsonEO(dims, float(r.uniform(0.12, 0.135)), torch.from_numpy(Uh).to(dev),
+                                prec="f32"))
+        p_ = gen.gaussian_spinor(dims, seed=seed + 20)[0]
+        xs.append(torch.from_numpy(np.ascontiguousarray(np.moveaxis(p_, 0, -1)).astype(np.complex64)).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+        sites += int(np.prod(dims))
+        del Uh
+    hs = [o.handle for o in ops]
+    ms_b = timed(lambda: weo.wilson_eo_apply_batch(hs, ys, xs, False, stream), 50, stream)
+    ms_s = timed(lambda: [weo.wilson_eo_apply(o.handle, yy, xx, 1, stream)
+                          for o, yy, xx in zip(ops, ys, xs)], 50, stream)
+    out["batch_16_24_32_f32"] = {"ms_one_launch": round(ms_b, 4), "ms_separate_applies": round(ms_s, 4),
+                                 "gflops_one_launch": round(FLOP_PER_SITE * sites / (ms_b * 1e-3) / 1e9, 1)}
+    for o in ops:
+        o.close()
+    return out
+
+
+def solve_comparison(dev, dims):
+    """Solve M^dag M x = b to true relative residual 1e-10 at kappa = 0.135 with
+    exp(i 0.4 H) links: FP16-storage mixed CG vs plain FP64 CG, same GPU."""
+    import torch
+
+    import gen
+    import paper_2303_08609_gb300 as weo
+
+    t0 = time.perf_counter()
+    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    b = gen.gaussian_spinor(dims, seed=1)[0]
+    gen_s = time.perf_counter() - t0
+    Ud = torch.from_numpy(U).to(dev)
+    del U
+    bd = torch.from_numpy(np.ascontiguousarray(np.moveaxis(b, 0, -1))).to(dev)
+    del b
+    res = {"lattice": list(dims), "kappa": 0.135, "tol": 1e-10, "field_gen_s": round(gen_s, 1)}
+    for name, prec, mixed in (("mixed_f16", "f16", True), ("mixed_bf16", "bf16", True),
+                              ("mixed_f32", "f32", True), ("plain_f64", "f64", False)):
+        op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=18)
+        x, info = op.solve(bd, tol=1e-10, maxiter=20000, mixed=mixed)
+        res[name] = {k: (round(v, 4) if isinstance(v, float) and k == "seconds" else v)
+                     for k, v in info.items()}
+        op.close()
+        del x
+        torch.cuda.empty_cache()
+    if res["plain_f64"]["converged"] and res["mixed_f16"]["converged"]:
+        res["speedup_f16_vs_f64"] = round(res["plain_f64"]["seconds"] / res["mixed_f16"]["seconds"], 2)
+    return res
 
 
 def cpu_baseline(U, psi, reps=1):
@@ -429,6 +561,13 @@ def run_reference(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.only_solve:
+        import torch
+
+        torch.cuda.set_device(local)
+        print(json.dumps({"solve": solve_comparison(torch.device("cuda", local),
+                                                    tuple(args.solve_dims))}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

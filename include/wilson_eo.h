@@ -142,6 +142,109 @@ int wilson_eo_link_grad(wilson_eo_t h, void *grad, const void *g_e, const void *
 int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi_e,
                     void *stream);
 
+/* Solve M_eo^dag M_eo x_e = b_e (CG on the normal equations of the even
+ * system of Eq. 4; Sec. 2 notes the solver's cost is that of the matrix
+ * multiplication). x_e and b_e are canonical even spinors in complex128
+ * whatever the handle's precision; x_e holds the initial guess on entry and the
+ * solution on return.
+ *   mixed = 0: plain FP64 CG (FP64 operator, vectors and reductions).
+ *   mixed = 1: CG with the handle's low-precision operator (FP32 for FP64 and
+ *              FP32 handles, FP16/BF16 storage for 16-bit handles) and FP32
+ *              vectors, with reliable updates: whenever the iterated residual
+ *              has fallen by `delta` (default 0.1) the FP32 increment is added
+ *              to the FP64 solution and the residual is recomputed as b - A x
+ *              with the FP64 operator. Reductions accumulate in FP64.
+ * Convergence: |b - A x| / |b| <= tol with the residual recomputed in FP64 from
+ * the returned x (true_relres_out). Returns WEO_OK, WEO_ERR_NOT_CONVERGED
+ * (maxiter iterations done; x_e holds the last iterate), WEO_ERR_NONFINITE (NaN
+ * or Inf, or a non-positive <p, A p>; x_e is not written) or an argument / CUDA
+ * error. tol in (0, 1); maxiter >= 0. Blocks until done; the iterations run on
+ * a stream the handle owns after the work already queued on `stream` finished.
+ * Iterations are launched in chunks from a CUDA graph (see
+ * wilson_eo_solver_config); the host reads one scalar per chunk. */
+int wilson_eo_solve(wilson_eo_t h, void *x_e, const void *b_e, double tol, int maxiter, int mixed,
+                    int *iters_out, double *true_relres_out, void *stream);
+
+/* The full Wilson system D_W xi = eta (Eq. 2) through the even-odd route:
+ *   wilson_eo_prepare_source: rhs_e = eta_e - D_eo eta_o = eta_e + kappa H_eo eta_o
+ *                             (right-hand side of Eq. 4; D_ee = 1)
+ *   wilson_eo_reconstruct:    xi_o  = eta_o - D_oe xi_e  = eta_o + kappa H_oe xi_e
+ *                             (Eq. 5; D_oo = 1)
+ * Both take canonical single-parity spinors in the handle's spinor dtype
+ * (FP64 and FP32 handles; WEO_ERR_UNSUPPORTED for 16-bit) and are
+ * asynchronous for device arrays. */
+int wilson_eo_prepare_source(wilson_eo_t h, void *rhs_e, const void *eta_e, const void *eta_o,
+                             void *stream);
+int wilson_eo_reconstruct(wilson_eo_t h, void *xi_o, const void *eta_o, const void *xi_e,
+                          void *stream);
+
+/* Solve D_W xi = eta: prepare the even source with FP64 operators, solve
+ * M_eo^dag M_eo xi_e = M_eo^dag rhs_e with wilson_eo_solve (same `mixed`, tol,
+ * maxiter and status rules; xi_e holds the initial guess on entry), then
+ * reconstruct xi_o in FP64. All four arrays are complex128 canonical spinors
+ * (device or host). iters_out / relres_out describe the even solve (the odd
+ * equations hold exactly up to rounding). Blocks until done; allocates three
+ * temporary FP64 fields for the call. */
+int wilson_eo_solve_full(wilson_eo_t h, void *xi_e, void *xi_o, const void *eta_e,
+                         const void *eta_o, double tol, int maxiter, int mixed, int *iters_out,
+                         double *relres_out, void *stream);
+
+/* Solver settings: reliable-update threshold delta in (0, 1), iterations per
+ * chunk (>= 1; default 8), use_graphs 1/0 (default 1). A value outside its range
+ * leaves that setting unchanged. */
+int wilson_eo_solver_config(wilson_eo_t h, double delta, int chunk, int use_graphs);
+
+/* Statistics of the handle's last solve: low-precision (or FP64 in plain mode)
+ * CG iterations, reliable updates, FP64 operator applications (true
+ * residuals), wall seconds. Any pointer may be NULL. */
+int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
+                          int *fp64_applies, double *seconds);
+
+/* M_eo (dag = 0) or M_eo^dag on n lattices at once, in ONE persistent
+ * cooperative kernel launch: every lattice keeps its own extents, kappa and
+ * links (its handle); the launch covers all first hops (Eq. 1 onto odd sites),
+ * synchronises the grid, then all second hops with the diagonal term (Eq. 4).
+ *   n        1..24 handles, all FP64 or all FP32, one link format, created on
+ *            the current device, no handle twice
+ *   outs[k], ins[k]  device arrays: one canonical even spinor of lattice k
+ * Uses each handle's odd-site buffer. Asynchronous on `stream`. */
+int wilson_eo_apply_batch(int n, const wilson_eo_t *hs, void *const *outs,
+                          const void *const *ins, int dag, void *stream);
+
+/* Autotune the hopping-kernel launch configuration for M_eo on this handle
+ * with nrhs right-hand sides: every candidate (threads 64/128/192/256 per CTA;
+ * 1, 2 or 4 right-hand sides per thread for FP32 handles) is timed with CUDA
+ * events on `stream` and the fastest is kept (wilson_eo_get_launch). Results
+ * are cached per process by (GPU, extents, precision, link format, nrhs) and,
+ * if the environment variable WILSON_EO_TUNE_CACHE names a file, appended to it
+ * and read back by later processes. Allocates two temporary spinor fields.
+ * Any output pointer may be NULL. Blocks until done. */
+int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out, double *ms_out,
+                   void *stream);
+
+/* Choose how M_eo and M_eo^dag are computed for FP32, FP16 and BF16 handles
+ * (apply, apply_dag, force, and the inner operator of the mixed solver):
+ *   algo 0  two hop launches with the odd-site intermediate in HBM (default);
+ *   algo 1  one persistent launch for both hops of Eq. 4: CTAs take (hop,
+ *           t-slice, chunk) items in wavefront order and keep the odd-site
+ *           intermediate in a ring of `ring` t-slices (3..64; 0 keeps the
+ *           current value, default 8) that stays in L2; `threads` per CTA
+ *           128 or 256 (0 keeps the current value). FP32 spinors and
+ *           arithmetic; links in the handle's precision.
+ * Items wait for the items they depend on with bounded polling; if a wait ever
+ * gives up (about a second without progress), the kernel records an error
+ * that wilson_eo_check reports as WEO_ERR_TIMEOUT. FP64 handles: algo 1 gives
+ * WEO_ERR_UNSUPPORTED. */
+int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads);
+
+/* Wait for `stream` and report whether any fused launch of this handle since
+ * the previous check gave up a bounded wait (WEO_ERR_TIMEOUT: the outputs of
+ * those calls are invalid); clears the record. WEO_OK otherwise. */
+int wilson_eo_check(wilson_eo_t h, void *stream);
+
+/* Current launch configuration of the handle's hopping kernels. */
+int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block);
+
 /* Launch configuration of the hopping kernels for the handle's precision:
  * threads per block (32..256, a multiple of 32) and right-hand sides per
  * thread (1, 2 or 4; values other than 1 apply to FP32 handles only, where the

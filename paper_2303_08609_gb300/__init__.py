@@ -78,11 +78,17 @@ def _load():
         "wilson_eo_force": (I, [P, P, P, P, P]),
         "wilson_eo_link_grad": (I, [P, P, P, P, P]),
         "wilson_eo_solve": (I, [P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
+        "wilson_eo_solver_config": (I, [P, D, I, I]),
+        "wilson_eo_prepare_source": (I, [P, P, P, P, P]),
+        "wilson_eo_reconstruct": (I, [P, P, P, P, P]),
+        "wilson_eo_solve_full": (I, [P, P, P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
+        "wilson_eo_solve_stats": (I, [P, IP, IP, IP, ctypes.POINTER(D)]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(P), I, P]),
-        "wilson_eo_tune": (I, [P, I, P]),
-        "wilson_eo_apply_fused": (I, [P, P, P, I, I, P]),
-        "wilson_eo_apply_fused_noalloc": (I, [P, P, P, I, P]),
+        "wilson_eo_tune": (I, [P, I, IP, IP, ctypes.POINTER(D), P]),
+        "wilson_eo_get_launch": (I, [P, IP, IP]),
+        "wilson_eo_set_algorithm": (I, [P, I, I, I]),
+        "wilson_eo_check": (I, [P, P]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
         f = getattr(lib, name, None)
@@ -336,6 +342,16 @@ class WilsonEO:
         d = torch.empty_like(phi) if want_dphi else None
         wilson_eo_force(self._h, F, d, phi, stream)
         return F, d
+
+    def solve(self, b, x0=None, tol=1e-10, maxiter=10000, mixed=True, stream=None):
+        """x with M^dag M x = b (complex128 planar). Returns (x, info dict)."""
+        import torch
+
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        st, it, rr = wilson_eo_solve(self._h, x, b, tol, maxiter, mixed, stream)
+        info = wilson_eo_solve_stats(self._h)
+        info.update({"status": STATUS.get(st, st), "true_relres": rr, "converged": st == WEO_OK})
+        return x, info
 
     def set_gauge(self, gauge, stream=None):
         wilson_eo_set_gauge(self._h, gauge, stream=stream)

@@ -135,47 +135,64 @@ int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, c
     return st;
 }
 
-// M_eo (dag = false) or M_eo^dag on device pointers.
-int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s)
+// M_eo (dag = false) or M_eo^dag on device pointers, for a packed gauge field
+// in precision `prec`, with the odd-site intermediate in `tmp`. FP64 / FP32
+// operators read and write spinors of their own precision; 16-bit operators
+// read and write FP32 spinors and keep the intermediate in 16-bit.
+int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const void *in,
+             int nrhs, bool dag, cudaStream_t s)
 {
+    const int prec = g.prec;
+    if (h->algo == 1 && prec != WEO_F64) {
+        const long long ext32 = h->vh * 96;
+        for (int r = 0; r < nrhs; ++r)
+            WEO_TRY(meo_fused(h, g, static_cast<char *>(out) + r * ext32,
+                              static_cast<const char *>(in) + r * ext32, dag, s));
+        return WEO_OK;
+    }
     HopParams p = geom_params(h);
     p.nrhs = nrhs;
-    p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
-    p.gauge_pb = h->gauge.pb;
-    const long long ext = (long long)ext_spinor_bytes(h);
-    if (h->prec == WEO_F64 || h->prec == WEO_F32) {
-        WEO_TRY(h->tmp.ensure((size_t)ext * nrhs));
+    p.gauge = static_cast<const char *>(g.buf.ptr);
+    p.gauge_pb = g.pb;
+    const long long ext = h->vh * (prec == WEO_F64 ? 192 : 96);
+    if (prec == WEO_F64 || prec == WEO_F32) {
+        WEO_TRY(tmp.ensure((size_t)ext * nrhs));
         p.out_parity = 1;
         p.in = in;
         p.in_stride = ext;
-        p.out = h->tmp.ptr;
+        p.out = tmp.ptr;
         p.out_stride = ext;
-        WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, dag, false, p, s));
+        WEO_TRY(handle_hop(h, prec, g.fmt, IO_SAME, dag, false, p, s));
         p.out_parity = 0;
-        p.in = h->tmp.ptr;
+        p.in = tmp.ptr;
         p.out = out;
         p.x = in;
         p.x_stride = ext;
         p.a = -h->kappa * h->kappa;
-        return handle_hop(h, h->prec, h->fmt, IO_SAME, dag, true, p, s);
+        return handle_hop(h, prec, g.fmt, IO_SAME, dag, true, p, s);
     }
     const long long s16 = h->vh * spinor_site_bytes(SK_H16);
-    WEO_TRY(h->tmp.ensure((size_t)s16 * nrhs));
+    WEO_TRY(tmp.ensure((size_t)s16 * nrhs));
     p.out_parity = 1;
     p.in = in;
     p.in_stride = ext;
-    p.out = h->tmp.ptr;
+    p.out = tmp.ptr;
     p.out_stride = s16;
-    WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_TO16, dag, false, p, s));
+    WEO_TRY(handle_hop(h, prec, g.fmt, IO_TO16, dag, false, p, s));
     p.out_parity = 0;
-    p.in = h->tmp.ptr;
+    p.in = tmp.ptr;
     p.in_stride = s16;
     p.out = out;
     p.out_stride = ext;
     p.x = in;
     p.x_stride = ext;
     p.a = -h->kappa * h->kappa;
-    return handle_hop(h, h->prec, h->fmt, IO_FROM16, dag, true, p, s);
+    return handle_hop(h, prec, g.fmt, IO_FROM16, dag, true, p, s);
+}
+
+int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s)
+{
+    return meo_with(h, h->gauge, h->tmp, out, in, nrhs, dag, s);
 }
 
 static int apply_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, bool dag,
@@ -272,6 +289,35 @@ int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved
     return WEO_OK;
 }
 
+int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (algo != 0 && algo != 1) return set_error(WEO_ERR_ARG, "algo must be 0 (two launches) or 1 (fused)");
+    if (algo == 1 && h->prec == WEO_F64)
+        return set_error(WEO_ERR_UNSUPPORTED, "the fused M_eo has FP32 arithmetic only");
+    if (ring != 0 && (ring < 3 || ring > 64)) return set_error(WEO_ERR_ARG, "ring must be 0 or in 3..64");
+    if (threads != 0 && threads != 128 && threads != 256)
+        return set_error(WEO_ERR_ARG, "threads must be 0, 128 or 256");
+    h->algo = algo;
+    if (ring) h->fused_ring = ring;
+    if (threads) h->fused_threads = threads;
+    return WEO_OK;
+}
+
+int wilson_eo_check(wilson_eo_t h, void *stream)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        DeviceGuard dg(h->device);
+        unsigned int err = 0;
+        WEO_TRY(fused_take_error(h, static_cast<cudaStream_t>(stream), &err));
+        if (err) return set_error(WEO_ERR_TIMEOUT, "a bounded wait in the fused M_eo kernel gave up; results of the calls since the last check are invalid");
+        return WEO_OK;
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_check");
+    }
+}
+
 int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *prec,
                    int *linkfmt, double *kappa, size_t *device_bytes)
 {
@@ -285,7 +331,7 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
     if (device_bytes)
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
-                        h->even1.bytes + h->stage_in.bytes +
+                        h->even1.bytes + h->fused_tmp.bytes + h->fused_ctrl.bytes + h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
 }
@@ -399,6 +445,109 @@ int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi
     }
 }
 
+int wilson_eo_solve(wilson_eo_t h, void *x_e, const void *b_e, double tol, int maxiter, int mixed,
+                    int *iters_out, double *true_relres_out, void *stream)
+{
+    try {
+        if (iters_out) *iters_out = 0;
+        if (true_relres_out) *true_relres_out = -1.0;
+        if (!h || !x_e || !b_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (x_e == b_e) return set_error(WEO_ERR_ARG, "x_e must not alias b_e");
+        if (!(tol > 0.0) || tol >= 1.0) return set_error(WEO_ERR_ARG, "tol must be in (0, 1)");
+        if (maxiter < 0) return set_error(WEO_ERR_ARG, "maxiter must be >= 0");
+        DeviceGuard dg(h->device);
+        const bool xh = !is_device_pointer(x_e), bh = !is_device_pointer(b_e);
+        return solve_device(h, x_e, b_e, xh, bh, tol, maxiter, mixed, iters_out, true_relres_out,
+                            static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solve");
+    }
+}
+
+// out = x + kappa H in, in the handle's precision (prepare / reconstruct)
+static int source_op(wilson_eo_t h, void *out, const void *in_a, const void *in_b, bool prepare,
+                     void *stream)
+{
+    if (!h || !out || !in_a || !in_b) return set_error(WEO_ERR_ARG, "NULL handle or array");
+    if (h->prec != WEO_F64 && h->prec != WEO_F32)
+        return set_error(WEO_ERR_UNSUPPORTED, "needs an FP64 or FP32 handle");
+    if (out == in_a || out == in_b) return set_error(WEO_ERR_ARG, "output must not alias an input");
+    DeviceGuard dg(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t b = ext_spinor_bytes(h);
+    const void *a, *c;
+    void *o;
+    bool oh;
+    WEO_TRY(stage_in(h->stage_in, in_a, b, s, &a));
+    WEO_TRY(stage_in(h->even1, in_b, b, s, &c));
+    WEO_TRY(stage_out(h->stage_out, out, b, &o, &oh));
+    WEO_TRY(prepare ? prepare_source_device(h, o, a, c, s) : reconstruct_device(h, o, a, c, s));
+    if (!oh && (a != in_a || c != in_b)) WEO_CUDA(cudaStreamSynchronize(s));
+    return finish_out(out, o, b, oh, s);
+}
+
+int wilson_eo_prepare_source(wilson_eo_t h, void *rhs_e, const void *eta_e, const void *eta_o,
+                             void *stream)
+{
+    try {
+        return source_op(h, rhs_e, eta_e, eta_o, true, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_prepare_source");
+    }
+}
+
+int wilson_eo_reconstruct(wilson_eo_t h, void *xi_o, const void *eta_o, const void *xi_e,
+                          void *stream)
+{
+    try {
+        return source_op(h, xi_o, eta_o, xi_e, false, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_reconstruct");
+    }
+}
+
+int wilson_eo_solve_full(wilson_eo_t h, void *xi_e, void *xi_o, const void *eta_e,
+                         const void *eta_o, double tol, int maxiter, int mixed, int *iters_out,
+                         double *relres_out, void *stream)
+{
+    try {
+        if (iters_out) *iters_out = 0;
+        if (relres_out) *relres_out = -1.0;
+        if (!h || !xi_e || !xi_o || !eta_e || !eta_o) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        const void *ptrs[4] = {xi_e, xi_o, eta_e, eta_o};
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < i; ++j)
+                if (ptrs[i] == ptrs[j]) return set_error(WEO_ERR_ARG, "arrays must not alias");
+        if (!(tol > 0.0) || tol >= 1.0) return set_error(WEO_ERR_ARG, "tol must be in (0, 1)");
+        if (maxiter < 0) return set_error(WEO_ERR_ARG, "maxiter must be >= 0");
+        DeviceGuard dg(h->device);
+        bool host[4];
+        for (int i = 0; i < 4; ++i) host[i] = !is_device_pointer(ptrs[i]);
+        return solve_full_device(h, xi_e, xi_o, eta_e, eta_o, host, tol, maxiter, mixed, iters_out,
+                                 relres_out, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solve_full");
+    }
+}
+
+int wilson_eo_solver_config(wilson_eo_t h, double delta, int chunk, int use_graphs)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        DeviceGuard dg(h->device);
+        return solver_configure(h, delta, chunk, use_graphs);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solver_config");
+    }
+}
+
+int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
+                          int *fp64_applies, double *seconds)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    return solver_stats(h, iterations, reliable_updates, fp64_applies, seconds);
+}
+
 void wilson_eo_destroy(wilson_eo_t h)
 {
     if (!h) return;
@@ -415,6 +564,9 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->stage_in.release();
     h->stage_out.release();
     h->stage_aux.release();
+    h->fused_tmp.release();
+    h->fused_ctrl.release();
+    solver_destroy(h);
     prof_destroy(h);
     delete h;
 }

@@ -1,0 +1,143 @@
+// Mixed-lattice batch: M_eo (or M_eo^dag) on several lattices -- each with its
+// own extents, kappa and links -- in ONE persistent cooperative launch. The grid
+// (a whole number of CTAs per SM, all resident) walks the CTA-sized tiles of
+// every lattice's first hop, synchronises once across the grid, then walks the
+// tiles of every second hop (with the axpy of Eq. 4). Lattices need not have a
+// size that fills the GPU on its own: small and large lattices share one launch.
+#include <cooperative_groups.h>
+
+#include <vector>
+
+#include "weo_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace weo {
+
+constexpr int kMaxBatch = 24;
+constexpr int kBatchThreads = 128;
+
+struct BatchArgs {
+    int n;
+    long long tile_begin[kMaxBatch + 1];  // prefix sums of CTA tiles per lattice
+    HopParams first[kMaxBatch];           // H_oe onto odd sites
+    HopParams second[kMaxBatch];          // in - kappa^2 H_eo tmp onto even sites
+};
+
+__device__ __forceinline__ int find_lattice(const BatchArgs &a, long long tile)
+{
+    int k = 0;
+    while (k + 1 < a.n && tile >= a.tile_begin[k + 1]) ++k;
+    return k;
+}
+
+template <class Sp, class Lk, bool Dag>
+__global__ void __launch_bounds__(kBatchThreads) batch_meo_kernel(const __grid_constant__ BatchArgs a)
+{
+    const long long total = a.tile_begin[a.n];
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int k = find_lattice(a, tile);
+        const long long site = (tile - a.tile_begin[k]) * kBatchThreads + threadIdx.x;
+        if (site < a.first[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, false, 1>(a.first[k], (int)site, 0);
+    }
+    cg::this_grid().sync();
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int k = find_lattice(a, tile);
+        const long long site = (tile - a.tile_begin[k]) * kBatchThreads + threadIdx.x;
+        if (site < a.second[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, true, 1>(a.second[k], (int)site, 0);
+    }
+}
+
+template <class Sp, class Lk, bool Dag>
+static int launch_batch(const BatchArgs &a, cudaStream_t s)
+{
+    auto kern = batch_meo_kernel<Sp, Lk, Dag>;
+    int dev = 0, sms = 0, per_sm = 0;
+    WEO_CUDA(cudaGetDevice(&dev));
+    WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0));
+    if (per_sm < 1) return set_error(WEO_ERR_CUDA, "batch kernel cannot be resident");
+    long long grid = (long long)sms * per_sm;
+    if (grid > a.tile_begin[a.n]) grid = a.tile_begin[a.n];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    WEO_CUDA(cudaLaunchKernelEx(&cfg, kern, a));
+    return WEO_OK;
+}
+
+template <class Sp, class Lk>
+static int launch_batch_dag(const BatchArgs &a, bool dag, cudaStream_t s)
+{
+    return dag ? launch_batch<Sp, Lk, true>(a, s) : launch_batch<Sp, Lk, false>(a, s);
+}
+
+}  // namespace weo
+
+using namespace weo;
+
+extern "C" int wilson_eo_apply_batch(int n, const wilson_eo_t *hs, void *const *outs,
+                                     const void *const *ins, int dag, void *stream)
+{
+    try {
+        if (n < 1 || n > kMaxBatch) return set_error(WEO_ERR_ARG, "batch size must be in 1..24");
+        if (!hs || !outs || !ins) return set_error(WEO_ERR_ARG, "NULL array of handles or fields");
+        const int prec = hs[0] ? hs[0]->prec : -1, fmt = hs[0] ? hs[0]->fmt : -1;
+        int dev = 0;
+        WEO_CUDA(cudaGetDevice(&dev));
+        for (int k = 0; k < n; ++k) {
+            if (!hs[k] || !outs[k] || !ins[k]) return set_error(WEO_ERR_ARG, "NULL handle or field in batch");
+            if (hs[k]->prec != prec || hs[k]->fmt != fmt)
+                return set_error(WEO_ERR_UNSUPPORTED, "a batch needs one precision and link format");
+            if (hs[k]->device != dev) return set_error(WEO_ERR_ARG, "batch handles must live on the current device");
+            if (outs[k] == ins[k]) return set_error(WEO_ERR_ARG, "out must not alias in");
+            for (int j = 0; j < k; ++j)
+                if (hs[j] == hs[k]) return set_error(WEO_ERR_ARG, "a handle appears twice in the batch");
+        }
+        if (prec != WEO_F32 && prec != WEO_F64)
+            return set_error(WEO_ERR_UNSUPPORTED, "batches are provided for FP64 and FP32 handles");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        BatchArgs a;
+        memset(&a, 0, sizeof(a));
+        a.n = n;
+        a.tile_begin[0] = 0;
+        for (int k = 0; k < n; ++k) {
+            wilson_eo_s *h = hs[k];
+            const long long ext = h->vh * (prec == WEO_F64 ? 192 : 96);
+            WEO_TRY(h->tmp.ensure((size_t)ext));
+            HopParams p = geom_params(h);
+            p.nrhs = 1;
+            p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
+            p.gauge_pb = h->gauge.pb;
+            p.in_stride = p.out_stride = p.x_stride = ext;
+            p.out_parity = 1;
+            p.in = ins[k];
+            p.out = h->tmp.ptr;
+            a.first[k] = p;
+            p.out_parity = 0;
+            p.in = h->tmp.ptr;
+            p.out = outs[k];
+            p.x = ins[k];
+            p.a = -h->kappa * h->kappa;
+            a.second[k] = p;
+            a.tile_begin[k + 1] = a.tile_begin[k] + (h->vh + kBatchThreads - 1) / kBatchThreads;
+        }
+        const bool c = fmt == WEO_LINK12;
+        int tok = prof_begin(hs[0], "batch_meo", s);
+        int st;
+        if (prec == WEO_F64)
+            st = c ? launch_batch_dag<SpF64, LkF64_12>(a, dag != 0, s) : launch_batch_dag<SpF64, LkF64_18>(a, dag != 0, s);
+        else
+            st = c ? launch_batch_dag<SpF32, LkF32_12>(a, dag != 0, s) : launch_batch_dag<SpF32, LkF32_18>(a, dag != 0, s);
+        prof_end(hs[0], tok, s);
+        return st;
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply_batch");
+    }
+}

@@ -7,7 +7,9 @@ namespace weo {
 template <class Lk>
 static int f32_rhs(bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
-    switch (cfg.rhs_block) {
+    int r = cfg.rhs_block;
+    while (r > 1 && r > p.nrhs) r /= 2;  // never more right-hand sides per thread than exist
+    switch (r) {
     case 4: return launch_da<SpF32, SpF32, SpF32, Lk, 4>(dag, axpy, p, cfg, s);
     case 2: return launch_da<SpF32, SpF32, SpF32, Lk, 2>(dag, axpy, p, cfg, s);
     default: return launch_da<SpF32, SpF32, SpF32, Lk, 1>(dag, axpy, p, cfg, s);

@@ -1,0 +1,671 @@
+// Solvers for M_eo^dag M_eo x = b (the normal equations of Eq. 4's even system;
+// the paper's Sec. 2 notes that the solver's speed is set by the matrix
+// multiplication).
+//
+//  * plain FP64 conjugate gradient: every vector, operator and reduction in FP64;
+//  * mixed precision: CG iterated with an FP32 or 16-bit-storage operator and
+//    FP32 vectors, with reliable updates (Clark et al., "Solving lattice QCD
+//    systems of equations using mixed precision solvers on GPUs", 2010): when
+//    the iterated residual has dropped by `delta` since the last update, the
+//    low-precision solution increment is added to the FP64 solution, and the
+//    residual is recomputed from scratch in FP64 as b - A x with the FP64
+//    operator. The search direction is kept. Convergence is declared on that
+//    FP64 true residual only.
+//
+// All scalars (rho, alpha, beta) live on the device: the last block of each
+// reduction finishes it and derives the next scalar, so an iteration is a fixed
+// sequence of kernel launches with no host round trip. Iterations run in chunks
+// captured once as a CUDA graph and replayed; the host reads the residual norm
+// only between chunks. Reductions are deterministic (fixed grid, partial sums
+// added in block order).
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "weo_internal.h"
+
+namespace weo {
+
+constexpr int kRedBlocks = 1024;
+constexpr int kRedThreads = 256;
+
+struct SolveScalars {
+    double rr;       // |r|^2 of the iterated residual
+    double pAp;      // Re <p, A p>
+    double alpha;
+    double beta;
+    double red;      // result of the last plain reduction
+    int nonfinite;   // set when a reduction or a scalar is NaN / Inf or pAp <= 0
+    unsigned int counter;
+    double partial[kRedBlocks];
+};
+
+struct SolverState {
+    Buffer scal;                 // SolveScalars on the device
+    SolveScalars *host = nullptr;  // pinned mirror of the leading scalars
+    Buffer x64, b64, r64, e64, t64, odd64;     // FP64 work vectors
+    Buffer xs, rs, p, Ap, t32, oddlo;          // low-precision work vectors
+    Buffer p64, Ap64;                          // plain FP64 CG
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [mixed]
+    int graph_chunk[2] = {0, 0};
+    double delta = 0.1;
+    int chunk = 8;
+    int use_graphs = 1;
+    // statistics of the last solve
+    int iterations = 0, reliable_updates = 0, hi_applies = 0;
+    double seconds = 0.0;
+};
+
+// ---------------------------------------------------------------- kernels --
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (int)threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;  // valid in thread 0
+}
+
+// Store this block's partial; the last block sums all partials in block order.
+// Returns true in every thread of the last block; *total is valid in thread 0.
+__device__ __forceinline__ bool finish_reduction(SolveScalars *sc, double block_val, double *total)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        sc->partial[blockIdx.x] = block_val;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(&sc->counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+        v += reinterpret_cast<volatile double *>(sc->partial)[k];
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+        *total = v;
+        sc->counter = 0;
+    }
+    return true;
+}
+
+template <typename T2>
+__device__ __forceinline__ double re_dot(T2 a, T2 b) { return double(a.x) * b.x + double(a.y) * b.y; }
+
+// mode 0: sc->red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp
+template <typename T2>
+__global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, long long n,
+                                                     SolveScalars *sc, int mode)
+{
+    double v = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        v += re_dot(a[k], b[k]);
+    v = block_sum(v);
+    double tot;
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
+        if (mode == 0) {
+            sc->red = tot;
+        } else {
+            sc->pAp = tot;
+            sc->alpha = sc->rr / tot;
+            if (!isfinite(tot) || !(tot > 0.0) || !isfinite(sc->alpha)) sc->nonfinite = 1;
+        }
+    }
+}
+
+// mode 0: sc->red = |a|^2;  mode 1: sc->rr = |a|^2
+template <typename T2>
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n, SolveScalars *sc,
+                                                       int mode)
+{
+    double v = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        v += re_dot(a[k], a[k]);
+    v = block_sum(v);
+    double tot;
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
+        if (mode == 0) sc->red = tot;
+        else sc->rr = tot;
+        if (!isfinite(tot)) sc->nonfinite = 1;
+    }
+}
+
+// x += alpha p ; r -= alpha Ap ; rr_new = |r|^2 ; beta = rr_new / rr ; rr = rr_new
+template <typename T2>
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T2 *p, const T2 *Ap,
+                                                           long long n, SolveScalars *sc)
+{
+    using T = decltype(T2().x);
+    const T alpha = T(sc->alpha);
+    double v = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        T2 xv = x[k], rv = r[k];
+        const T2 pv = p[k], av = Ap[k];
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        rv.x -= alpha * av.x;
+        rv.y -= alpha * av.y;
+        x[k] = xv;
+        r[k] = rv;
+        v += re_dot(rv, rv);
+    }
+    v = block_sum(v);
+    double tot;
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
+        sc->beta = tot / sc->rr;
+        sc->rr = tot;
+        if (!isfinite(tot) || !isfinite(sc->beta)) sc->nonfinite = 1;
+    }
+}
+
+// p = r + beta p
+template <typename T2>
+__global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *sc)
+{
+    using T = decltype(T2().x);
+    const T beta = T(sc->beta);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        T2 pv = p[k];
+        const T2 rv = r[k];
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        p[k] = pv;
+    }
+}
+
+// r = b - t ; sc->red = |r|^2
+__global__ void __launch_bounds__(kRedThreads) k_residual(double2 *r, const double2 *b,
+                                                          const double2 *t, long long n,
+                                                          SolveScalars *sc)
+{
+    double v = 0.0;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        double2 rv = make_double2(b[k].x - t[k].x, b[k].y - t[k].y);
+        r[k] = rv;
+        v += rv.x * rv.x + rv.y * rv.y;
+    }
+    v = block_sum(v);
+    double tot;
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
+        sc->red = tot;
+        if (!isfinite(tot)) sc->nonfinite = 1;
+    }
+}
+
+template <typename D2, typename S2>
+__global__ void k_convert(D2 *d, const S2 *s, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const S2 v = s[k];
+        D2 o;
+        o.x = v.x;
+        o.y = v.y;
+        d[k] = o;
+    }
+}
+
+// x64 += xs ; xs = 0
+__global__ void k_accumulate(double2 *x, float2 *xs, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float2 v = xs[k];
+        double2 a = x[k];
+        a.x += v.x;
+        a.y += v.y;
+        x[k] = a;
+        xs[k] = make_float2(0.f, 0.f);
+    }
+}
+
+static unsigned red_grid(long long n)
+{
+    long long b = (n + kRedThreads - 1) / kRedThreads;
+    return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
+}
+
+// ------------------------------------------------------------------ state --
+
+void solver_destroy(wilson_eo_s *h)
+{
+    SolverState *S = h->solver;
+    if (!S) return;
+    for (auto &g : S->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    if (S->host) cudaFreeHost(S->host);
+    Buffer *bufs[] = {&S->scal, &S->x64, &S->b64, &S->r64, &S->e64, &S->t64, &S->odd64,
+                      &S->xs, &S->rs, &S->p, &S->Ap, &S->t32, &S->oddlo, &S->p64, &S->Ap64};
+    for (Buffer *b : bufs) b->release();
+    delete S;
+    h->solver = nullptr;
+}
+
+static int solver_state(wilson_eo_s *h, SolverState **out)
+{
+    if (!h->solver) {
+        SolverState *S = new SolverState();
+        h->solver = S;
+        cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
+        e = cudaMallocHost(&S->host, sizeof(SolveScalars));
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMallocHost", __FILE__, __LINE__);
+        WEO_TRY(S->scal.ensure(sizeof(SolveScalars)));
+        WEO_CUDA(cudaMemsetAsync(S->scal.ptr, 0, sizeof(SolveScalars), S->stream));
+    }
+    *out = h->solver;
+    return WEO_OK;
+}
+
+static SolveScalars *dev_scal(SolverState *S) { return static_cast<SolveScalars *>(S->scal.ptr); }
+
+static int read_scalars(SolverState *S)
+{
+    WEO_CUDA(cudaMemcpyAsync(S->host, S->scal.ptr, offsetof(SolveScalars, counter), cudaMemcpyDeviceToHost,
+                             S->stream));
+    WEO_CUDA(cudaStreamSynchronize(S->stream));
+    return WEO_OK;
+}
+
+// FP64 packed gauge for true residuals (the handle's own if it is FP64)
+static int hi_gauge(wilson_eo_s *h, const PackedGauge **g, cudaStream_t s)
+{
+    if (h->prec == WEO_F64) {
+        *g = &h->gauge;
+        return WEO_OK;
+    }
+    if (!h->gauge_f64.valid)
+        WEO_TRY(pack_gauge(h, h->gauge_f64, WEO_F64, WEO_LINK18, h->canon_gauge.ptr, h->canon_is_f64, s));
+    *g = &h->gauge_f64;
+    return WEO_OK;
+}
+
+// low-precision operator for the mixed solver: FP32 for an FP64 handle
+static int lo_gauge(wilson_eo_s *h, const PackedGauge **g, cudaStream_t s)
+{
+    if (h->prec != WEO_F64) {
+        *g = &h->gauge;
+        return WEO_OK;
+    }
+    if (!h->gauge_lo.valid)
+        WEO_TRY(pack_gauge(h, h->gauge_lo, WEO_F32, h->fmt, h->canon_gauge.ptr, h->canon_is_f64, s));
+    *g = &h->gauge_lo;
+    return WEO_OK;
+}
+
+// A v = M^dag (M v) with gauge g; e: even temporary, odd: odd temporary
+static int normal_op(wilson_eo_s *h, const PackedGauge &g, Buffer &odd, void *e, void *out,
+                     const void *v, cudaStream_t s)
+{
+    WEO_TRY(meo_with(h, g, odd, e, v, 1, false, s));
+    return meo_with(h, g, odd, out, e, 1, true, s);
+}
+
+// One CG iteration. mixed: low-precision vectors (float2) with operator glo;
+// otherwise FP64 vectors with operator ghi.
+static int cg_iteration(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bool mixed,
+                        cudaStream_t s)
+{
+    const long long n = 12 * h->vh;
+    const unsigned grid = red_grid(n);
+    SolveScalars *sc = dev_scal(S);
+    if (mixed) {
+        WEO_TRY(normal_op(h, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
+        k_dot<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc, 1);
+        k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->rs.ptr,
+                                                          (const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc);
+        k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->p.ptr, (const float2 *)S->rs.ptr, n, sc);
+    } else {
+        WEO_TRY(normal_op(h, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
+        k_dot<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc, 1);
+        k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->r64.ptr,
+                                                           (const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
+        k_cg_dir<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->p64.ptr, (const double2 *)S->r64.ptr, n, sc);
+    }
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
+// Run `k` iterations, from a captured graph when enabled.
+static int cg_chunk(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bool mixed, int k)
+{
+    cudaStream_t s = S->stream;
+    if (!S->use_graphs) {
+        for (int i = 0; i < k; ++i) WEO_TRY(cg_iteration(h, S, g, mixed, s));
+        return WEO_OK;
+    }
+    const int gi = mixed ? 1 : 0;
+    if (!S->graph[gi] || S->graph_chunk[gi] != k) {
+        if (S->graph[gi]) {
+            cudaGraphExecDestroy(S->graph[gi]);
+            S->graph[gi] = nullptr;
+        }
+        // profiling events are not recorded into the graph
+        Profiler *saved = h->prof;
+        h->prof = nullptr;
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            h->prof = saved;
+            return fail_cuda(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+        }
+        int st = WEO_OK;
+        for (int i = 0; i < k && st == WEO_OK; ++i) st = cg_iteration(h, S, g, mixed, s);
+        e = cudaStreamEndCapture(s, &graph);
+        h->prof = saved;
+        if (st != WEO_OK) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        e = cudaGraphInstantiate(&S->graph[gi], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            S->graph[gi] = nullptr;
+            return fail_cuda(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        }
+        S->graph_chunk[gi] = k;
+    }
+    WEO_CUDA(cudaGraphLaunch(S->graph[gi], s));
+    return WEO_OK;
+}
+
+// r64 = b64 - A x64 with the FP64 operator; returns |r|^2 in S->host->red
+static int true_residual(wilson_eo_s *h, SolverState *S, const PackedGauge &ghi)
+{
+    cudaStream_t s = S->stream;
+    const long long n = 12 * h->vh;
+    WEO_TRY(normal_op(h, ghi, S->odd64, S->e64.ptr, S->t64.ptr, S->x64.ptr, s));
+    k_residual<<<red_grid(n), kRedThreads, 0, s>>>((double2 *)S->r64.ptr, (const double2 *)S->b64.ptr,
+                                                    (const double2 *)S->t64.ptr, n, dev_scal(S));
+    WEO_CUDA(cudaGetLastError());
+    S->hi_applies += 1;
+    return read_scalars(S);
+}
+
+static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *iters_out,
+                      double *relres_out)
+{
+    SolverState *S = h->solver;
+    cudaStream_t s = S->stream;
+    const long long n = 12 * h->vh;
+    const size_t b64 = (size_t)n * 16, b32 = (size_t)n * 8;
+    const unsigned grid = red_grid(n);
+    SolveScalars *sc = dev_scal(S);
+    const PackedGauge *ghi = nullptr, *glo = nullptr;
+    WEO_TRY(hi_gauge(h, &ghi, s));
+    WEO_TRY(S->r64.ensure(b64));
+    WEO_TRY(S->e64.ensure(b64));
+    WEO_TRY(S->t64.ensure(b64));
+    WEO_TRY(S->odd64.ensure(b64));
+    WEO_CUDA(cudaMemsetAsync(sc, 0, offsetof(SolveScalars, partial), s));
+    S->iterations = S->reliable_updates = S->hi_applies = 0;
+
+    // |b|^2
+    k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->b64.ptr, n, sc, 0);
+    WEO_CUDA(cudaGetLastError());
+    WEO_TRY(read_scalars(S));
+    const double bb = S->host->red;
+    if (!(bb > 0.0) || !isfinite(bb)) {
+        if (bb == 0.0) {  // b = 0: x = 0 is exact
+            WEO_CUDA(cudaMemsetAsync(S->x64.ptr, 0, b64, s));
+            if (iters_out) *iters_out = 0;
+            if (relres_out) *relres_out = 0.0;
+            return WEO_OK;
+        }
+        return set_error(WEO_ERR_NONFINITE, "non-finite right-hand side");
+    }
+    const double target = tol * tol * bb;
+
+    WEO_TRY(true_residual(h, S, *ghi));
+    double rr_true = S->host->red;
+    int status = WEO_ERR_NOT_CONVERGED;
+    if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite initial residual");
+
+    if (!mixed) {
+        WEO_TRY(S->p64.ensure(b64));
+        WEO_TRY(S->Ap64.ensure(b64));
+        WEO_CUDA(cudaMemcpyAsync(S->p64.ptr, S->r64.ptr, b64, cudaMemcpyDeviceToDevice, s));
+        k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->r64.ptr, n, sc, 1);
+        WEO_CUDA(cudaGetLastError());
+        double rr = rr_true;
+        if (rr <= target) status = WEO_OK;
+        while (status != WEO_OK && S->iterations < maxiter) {
+            const int k = std::min(S->chunk, maxiter - S->iterations);
+            WEO_TRY(cg_chunk(h, S, *ghi, false, k));
+            S->iterations += k;
+            WEO_TRY(read_scalars(S));
+            if (S->host->nonfinite) return set_error(WEO_ERR_NONFINITE, "non-finite value in FP64 CG");
+            rr = S->host->rr;
+            if (rr <= target) {
+                // confirm on the recomputed residual; restart from it if not met
+                WEO_TRY(true_residual(h, S, *ghi));
+                rr_true = S->host->red;
+                if (rr_true <= target) {
+                    status = WEO_OK;
+                    break;
+                }
+                WEO_CUDA(cudaMemcpyAsync(S->p64.ptr, S->r64.ptr, b64, cudaMemcpyDeviceToDevice, s));
+                k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->r64.ptr, n, sc, 1);
+                WEO_CUDA(cudaGetLastError());
+            }
+        }
+    } else {
+        WEO_TRY(lo_gauge(h, &glo, s));
+        WEO_TRY(S->xs.ensure(b32));
+        WEO_TRY(S->rs.ensure(b32));
+        WEO_TRY(S->p.ensure(b32));
+        WEO_TRY(S->Ap.ensure(b32));
+        WEO_TRY(S->t32.ensure(b32));
+        WEO_CUDA(cudaMemsetAsync(S->xs.ptr, 0, b32, s));
+        k_convert<float2, double2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, n);
+        WEO_CUDA(cudaMemcpyAsync(S->p.ptr, S->rs.ptr, b32, cudaMemcpyDeviceToDevice, s));
+        k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->rs.ptr, n, sc, 1);
+        WEO_CUDA(cudaGetLastError());
+        double r_max = sqrt(rr_true);
+        if (rr_true <= target) status = WEO_OK;
+        while (status != WEO_OK && S->iterations < maxiter) {
+            const int k = std::min(S->chunk, maxiter - S->iterations);
+            WEO_TRY(cg_chunk(h, S, *glo, true, k));
+            S->iterations += k;
+            WEO_TRY(read_scalars(S));
+            if (S->host->nonfinite)
+                return set_error(WEO_ERR_NONFINITE, "non-finite value in the low-precision CG");
+            const double rr = S->host->rr;
+            const bool update = sqrt(rr) < S->delta * r_max || rr <= target || S->iterations >= maxiter;
+            if (!update) continue;
+            // reliable update: fold the increment into x and recompute r in FP64
+            k_accumulate<<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (float2 *)S->xs.ptr, n);
+            WEO_CUDA(cudaGetLastError());
+            WEO_TRY(true_residual(h, S, *ghi));
+            S->reliable_updates += 1;
+            rr_true = S->host->red;
+            if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
+            if (rr_true <= target) {
+                status = WEO_OK;
+                break;
+            }
+            r_max = sqrt(rr_true);
+            k_convert<float2, double2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, n);
+            k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->rs.ptr, n, sc, 1);
+            WEO_CUDA(cudaGetLastError());
+        }
+    }
+    if (status != WEO_OK) {
+        // report the residual of the returned iterate
+        WEO_TRY(true_residual(h, S, *ghi));
+        rr_true = S->host->red;
+        set_error(WEO_ERR_NOT_CONVERGED, "maxiter reached before the true residual met tol");
+    }
+    if (iters_out) *iters_out = S->iterations;
+    if (relres_out) *relres_out = sqrt(rr_true / bb);
+    return status;
+}
+
+int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs)
+{
+    SolverState *S;
+    WEO_TRY(solver_state(h, &S));
+    if (delta > 0.0 && delta < 1.0) S->delta = delta;
+    if (chunk >= 1) S->chunk = chunk;
+    if (use_graphs >= 0) S->use_graphs = use_graphs ? 1 : 0;
+    for (auto &g : S->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    return WEO_OK;
+}
+
+int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host,
+                 double tol, int maxiter, int mixed, int *iters_out, double *relres_out,
+                 cudaStream_t user)
+{
+    SolverState *S;
+    WEO_TRY(solver_state(h, &S));
+    const size_t b64 = (size_t)12 * h->vh * 16;
+    WEO_TRY(S->x64.ensure(b64));
+    WEO_TRY(S->b64.ensure(b64));
+    // every buffer an iteration touches exists before a graph is captured
+    WEO_TRY(S->oddlo.ensure((size_t)h->vh * 96));
+    WEO_TRY(S->odd64.ensure(b64));
+    // order after the caller's prior work, then run on the solver's own stream
+    WEO_CUDA(cudaStreamSynchronize(user));
+    cudaStream_t s = S->stream;
+    WEO_CUDA(cudaMemcpyAsync(S->x64.ptr, x_e, b64,
+                             x_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    WEO_CUDA(cudaMemcpyAsync(S->b64.ptr, b_e, b64,
+                             b_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    auto t0 = std::chrono::steady_clock::now();
+    int st = solve_impl(h, tol, maxiter, mixed, iters_out, relres_out);
+    if (st == WEO_OK || st == WEO_ERR_NOT_CONVERGED) {
+        cudaError_t e = cudaMemcpyAsync(x_e, S->x64.ptr, b64,
+                                        x_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi_applies,
+                 double *seconds)
+{
+    SolverState *S = h->solver;
+    if (iterations) *iterations = S ? S->iterations : 0;
+    if (reliable_updates) *reliable_updates = S ? S->reliable_updates : 0;
+    if (hi_applies) *hi_applies = S ? S->hi_applies : 0;
+    if (seconds) *seconds = S ? S->seconds : 0.0;
+    return WEO_OK;
+}
+
+}  // namespace weo
+
+// ------------------------------------------------- full system (Eqs. 3-5) --
+namespace weo {
+
+// out = x + a * H_{po} in with gauge g (precision g.prec, spinors of that precision)
+static int hop_axpy(wilson_eo_s *h, const PackedGauge &g, int out_parity, void *out,
+                    const void *in, const void *x, double a, cudaStream_t s)
+{
+    HopParams p = geom_params(h);
+    p.nrhs = 1;
+    p.gauge = static_cast<const char *>(g.buf.ptr);
+    p.gauge_pb = g.pb;
+    const long long ext = h->vh * (g.prec == WEO_F64 ? 192 : 96);
+    p.in_stride = p.out_stride = p.x_stride = ext;
+    p.out_parity = out_parity;
+    p.in = in;
+    p.out = out;
+    p.x = x;
+    p.a = a;
+    return handle_hop(h, g.prec, g.fmt, IO_SAME, false, true, p, s);
+}
+
+// rhs_e = eta_e - D_eo eta_o = eta_e + kappa H_eo eta_o   (right side of Eq. 4)
+int prepare_source_device(wilson_eo_s *h, void *rhs_e, const void *eta_e, const void *eta_o,
+                          cudaStream_t s)
+{
+    return hop_axpy(h, h->gauge, 0, rhs_e, eta_o, eta_e, h->kappa, s);
+}
+
+// xi_o = eta_o - D_oe xi_e = eta_o + kappa H_oe xi_e   (Eq. 5, D_oo = 1)
+int reconstruct_device(wilson_eo_s *h, void *xi_o, const void *eta_o, const void *xi_e,
+                       cudaStream_t s)
+{
+    return hop_axpy(h, h->gauge, 1, xi_o, xi_e, eta_o, h->kappa, s);
+}
+
+// D_W xi = eta through Eqs. 3-5, all FP64 except the mixed solver's inner CG.
+// Device or host complex128 arrays (flags say which).
+int solve_full_device(wilson_eo_s *h, void *xi_e, void *xi_o, const void *eta_e,
+                      const void *eta_o, const bool host[4], double tol, int maxiter, int mixed,
+                      int *iters_out, double *relres_out, cudaStream_t user)
+{
+    SolverState *S;
+    WEO_TRY(solver_state(h, &S));
+    cudaStream_t s = S->stream;
+    const size_t b64 = (size_t)12 * h->vh * 16;
+    WEO_CUDA(cudaStreamSynchronize(user));
+    const PackedGauge *ghi = nullptr;
+    WEO_TRY(hi_gauge(h, &ghi, s));
+    Buffer ee, eo, rhs;
+    int st = ee.ensure(b64);
+    if (st == WEO_OK) st = eo.ensure(b64);
+    if (st == WEO_OK) st = rhs.ensure(b64);
+    auto cleanup = [&]() { ee.release(); eo.release(); rhs.release(); };
+    if (st != WEO_OK) { cleanup(); return st; }
+    cudaMemcpyKind k2 = host[2] ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaMemcpyKind k3 = host[3] ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(ee.ptr, eta_e, b64, k2, s) != cudaSuccess ||
+        cudaMemcpyAsync(eo.ptr, eta_o, b64, k3, s) != cudaSuccess) {
+        cleanup();
+        return fail_cuda(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__);
+    }
+    // rhs = eta_e + kappa H_eo eta_o ; b = M^dag rhs (into ee, which is free now)
+    st = hop_axpy(h, *ghi, 0, rhs.ptr, eo.ptr, ee.ptr, h->kappa, s);
+    if (st == WEO_OK) st = S->odd64.ensure(b64);
+    if (st == WEO_OK) st = meo_with(h, *ghi, S->odd64, ee.ptr, rhs.ptr, 1, true, s);
+    if (st != WEO_OK) { cleanup(); return st; }
+    // even solve on device copies (x starts from the caller's xi_e guess)
+    if (cudaMemcpyAsync(rhs.ptr, xi_e, b64, host[0] ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        cleanup();
+        return fail_cuda(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__);
+    }
+    st = solve_device(h, rhs.ptr, ee.ptr, false, false, tol, maxiter, mixed, iters_out, relres_out, s);
+    if (st != WEO_OK && st != WEO_ERR_NOT_CONVERGED) { cleanup(); return st; }
+    const int solve_status = st;
+    // xi_o = eta_o + kappa H_oe xi_e  (into ee)
+    st = hop_axpy(h, *ghi, 1, ee.ptr, rhs.ptr, eo.ptr, h->kappa, s);
+    if (st == WEO_OK && cudaMemcpyAsync(xi_e, rhs.ptr, b64, host[0] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        st = fail_cuda(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__);
+    if (st == WEO_OK && cudaMemcpyAsync(xi_o, ee.ptr, b64, host[1] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        st = fail_cuda(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__);
+    if (st == WEO_OK && cudaStreamSynchronize(s) != cudaSuccess)
+        st = fail_cuda(cudaGetLastError(), "cudaStreamSynchronize", __FILE__, __LINE__);
+    cleanup();
+    return st == WEO_OK ? solve_status : st;
+}
+
+}  // namespace weo

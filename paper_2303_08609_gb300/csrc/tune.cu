@@ -1,0 +1,181 @@
+// Autotuner for the hopping kernels: times M_eo with each candidate launch
+// configuration (threads per CTA; right-hand sides per thread for FP32
+// handles) on the handle's own lattice and keeps the fastest. Results are
+// cached per process, keyed by (GPU name, extents, precision, link format,
+// nrhs), and optionally in a text file named by the environment variable
+// WILSON_EO_TUNE_CACHE (one "key threads rhs_block ms" line per entry).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "weo_internal.h"
+
+namespace weo {
+
+struct TuneEntry {
+    int threads, rhs_block;
+    double ms;
+};
+
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneEntry> g_tune_cache;
+static bool g_tune_file_loaded = false;
+
+static std::string tune_key(const wilson_eo_s *h, int nrhs)
+{
+    cudaDeviceProp prop;
+    char name[256] = "gpu";
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) {
+        strncpy(name, prop.name, sizeof(name) - 1);
+        name[sizeof(name) - 1] = '\0';
+        for (char *c = name; *c; ++c)
+            if (*c == ' ') *c = '_';
+    } else {
+        (void)cudaGetLastError();
+    }
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s:%dx%dx%dx%d:p%d:f%d:n%d", name, h->dims[0], h->dims[1],
+             h->dims[2], h->dims[3], h->prec, h->fmt, nrhs);
+    return buf;
+}
+
+static void load_tune_file()
+{
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = getenv("WILSON_EO_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[400];
+    TuneEntry e;
+    while (fscanf(f, "%399s %d %d %lf", key, &e.threads, &e.rhs_block, &e.ms) == 4)
+        g_tune_cache[key] = e;
+    fclose(f);
+}
+
+static void append_tune_file(const std::string &key, const TuneEntry &e)
+{
+    const char *path = getenv("WILSON_EO_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %.6f\n", key.c_str(), e.threads, e.rhs_block, e.ms);
+    fclose(f);
+}
+
+int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int *rhs_out,
+                double *ms_out)
+{
+    const std::string key = tune_key(h, nrhs);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        load_tune_file();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->cfg[h->prec].threads = it->second.threads;
+            h->cfg[h->prec].rhs_block = it->second.rhs_block;
+            if (threads_out) *threads_out = it->second.threads;
+            if (rhs_out) *rhs_out = it->second.rhs_block;
+            if (ms_out) *ms_out = it->second.ms;
+            return WEO_OK;
+        }
+    }
+    const size_t bytes = (size_t)h->vh * (h->prec == WEO_F64 ? 192 : 96) * nrhs;
+    Buffer in, out;
+    WEO_TRY(in.ensure(bytes));
+    int st = out.ensure(bytes);
+    if (st != WEO_OK) {
+        in.release();
+        return st;
+    }
+    // a non-trivial but cheap input: constant bytes
+    cudaMemsetAsync(in.ptr, 0x3c, bytes, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int> rb = {1};
+    if (h->prec == WEO_F32) {
+        if (nrhs >= 2) rb.push_back(2);
+        if (nrhs >= 4) rb.push_back(4);
+    }
+    const LaunchCfg saved = h->cfg[h->prec];
+    Profiler *saved_prof = h->prof;
+    h->prof = nullptr;
+    TuneEntry best = {saved.threads, saved.rhs_block, 1e30};
+    for (int threads : {64, 128, 192, 256}) {
+        for (int r : rb) {
+            h->cfg[h->prec].threads = threads;
+            h->cfg[h->prec].rhs_block = r;
+            bool ok = true;
+            for (int w = 0; w < 2 && ok; ++w) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
+            if (!ok) continue;
+            const int reps = 5;
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps && ok; ++k) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
+            cudaEventRecord(e1, s);
+            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best.ms) best = {threads, r, ms};
+        }
+    }
+    h->prof = saved_prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    in.release();
+    out.release();
+    if (best.ms >= 1e30) {
+        h->cfg[h->prec] = saved;
+        return set_error(WEO_ERR_CUDA, "no launch configuration ran");
+    }
+    h->cfg[h->prec].threads = best.threads;
+    h->cfg[h->prec].rhs_block = best.rhs_block;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+        append_tune_file(key, best);
+    }
+    if (threads_out) *threads_out = best.threads;
+    if (rhs_out) *rhs_out = best.rhs_block;
+    if (ms_out) *ms_out = best.ms;
+    return WEO_OK;
+}
+
+}  // namespace weo
+
+using namespace weo;
+
+extern "C" int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out,
+                              double *ms_out, void *stream)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        if (nrhs < 1) return set_error(WEO_ERR_ARG, "nrhs must be >= 1");
+        int prev = -1;
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
+        int st = tune_handle(h, nrhs, static_cast<cudaStream_t>(stream), threads_out, rhs_block_out, ms_out);
+        if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+        return st;
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_tune");
+    }
+}
+
+extern "C" int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (threads) *threads = h->cfg[h->prec].threads;
+    if (rhs_block) *rhs_block = h->cfg[h->prec].rhs_block;
+    return WEO_OK;
+}

@@ -117,13 +117,12 @@ __device__ __forceinline__ void hop_dir(cx<T> (&acc)[R][12], const HopParams &p,
     }
 }
 
+// All hops of output site i (parity p.out_parity) for right-hand sides
+// rhs0 .. rhs0+R-1, then the optional axpy and the store.
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
-__global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
+__device__ __forceinline__ void hop_site(const HopParams &p, const int i, const int rhs0)
 {
     using T = typename SOut::real;  // FP64 only when the output is FP64
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.vh) return;
-    const int rhs0 = blockIdx.y * R;
     constexpr int S0 = Dag ? -1 : 1;
 
     int rem = i;
@@ -179,6 +178,14 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
         }
         SOut::store(static_cast<char *>(p.out) + (rhs0 + r) * p.out_stride, p.vh, i, acc[r]);
     }
+}
+
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
+__global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.vh) return;
+    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, blockIdx.y * R);
 }
 
 }  // namespace weo

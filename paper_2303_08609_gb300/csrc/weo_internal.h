@@ -69,6 +69,7 @@ struct LaunchCfg {
 };
 
 struct Profiler;
+struct SolverState;
 
 }  // namespace weo
 
@@ -90,6 +91,13 @@ struct wilson_eo_s {
     weo::Buffer stage_in, stage_out, stage_aux;
     weo::LaunchCfg cfg[4];       // per spinor precision kind
     weo::Profiler *prof = nullptr;
+    weo::SolverState *solver = nullptr;
+    // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
+    int algo = 0;
+    int fused_ring = 8;
+    int fused_threads = 128;
+    weo::Buffer fused_tmp;   // ring of odd-site t-slices
+    weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
 };
 
 namespace weo {
@@ -121,12 +129,36 @@ std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axp
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
                cudaStream_t s);
 
+// M_eo / M_eo^dag with a given packed gauge field (its precision decides the
+// spinor formats) and odd-site buffer (api.cu)
+int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const void *in,
+             int nrhs, bool dag, cudaStream_t s);
+// fused.cu: single-launch M_eo with FP32 spinors; error word of bounded waits
+int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, bool dag,
+              cudaStream_t s);
+int fused_take_error(wilson_eo_s *h, cudaStream_t s, unsigned int *err);
 // M_eo / M_eo^dag on device arrays in the handle's external format (api.cu)
 int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s);
 // link gradient (force = 0) or force TA(G U^dag) (force = 1), force.cu
 int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, int force,
                      cudaStream_t s);
 int scale_spinor(wilson_eo_s *h, void *v, int nrhs, double c, cudaStream_t s);
+
+// solver.cu
+int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host,
+                 double tol, int maxiter, int mixed, int *iters_out, double *relres_out,
+                 cudaStream_t user);
+int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs);
+int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi_applies,
+                 double *seconds);
+void solver_destroy(wilson_eo_s *h);
+int prepare_source_device(wilson_eo_s *h, void *rhs_e, const void *eta_e, const void *eta_o,
+                          cudaStream_t s);
+int reconstruct_device(wilson_eo_s *h, void *xi_o, const void *eta_o, const void *xi_e,
+                       cudaStream_t s);
+int solve_full_device(wilson_eo_s *h, void *xi_e, void *xi_o, const void *eta_e,
+                      const void *eta_o, const bool host[4], double tol, int maxiter, int mixed,
+                      int *iters_out, double *relres_out, cudaStream_t user);
 
 // Pack a canonical gauge field (device memory) into `g` (allocates).
 int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *canon, int is_f64,
