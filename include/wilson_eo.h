@@ -261,6 +261,31 @@ int wilson_eo_profile(wilson_eo_t h, int enable);
 int wilson_eo_profile_read(wilson_eo_t h, int max_kernels, char *names, int name_len,
                            double *total_ms, long long *launches, int *n_kernels, int reset);
 
+/* M_eo in_e (dag = 0) or M_eo^dag in_e (dag = 1) in FP32 without allocating
+ * any memory. The paper has no counterpart: this entry point is for callers
+ * that cannot call cudaMalloc -- code whose device memory belongs to a
+ * framework's allocator, a real-time loop that must not enter the driver's
+ * allocator, a plug-in that is only handed buffers. It takes no handle (creating
+ * one allocates); the caller passes device arrays only:
+ *   dims   {Lx, Ly, Lz, Lt}, each even and >= 2, and V/2 <= 349525 sites;
+ *          larger lattices are rejected with WEO_ERR_DIMS and a message naming
+ *          the limit
+ *   gauge  canonical gauge field, complex64, device memory
+ *   in_e   one canonical FP32 even spinor (planar complex64), device memory
+ *   out_e  receives the result; must not alias in_e
+ * Host arrays are rejected with WEO_ERR_ARG (staging them would allocate).
+ * The odd-site intermediate H_oe in_e lives in a fixed 32 MiB array compiled
+ * into the library (a file-scope __device__ variable), which every GPU that
+ * loads the library holds until the process exits. The first call on a device
+ * looks up that array's device address for the current device; make that first
+ * call before any stream capture. All calls share the array and it keeps the
+ * last call's contents; nothing in it has to start at zero because each call
+ * writes every entry before reading it. Calls that overlap on the GPU (streams
+ * without ordering between them, or several host threads) race on the array:
+ * the caller must serialise them. Asynchronous on `stream`. */
+int wilson_eo_apply_noalloc(const int dims[4], double kappa, const void *gauge, void *out_e,
+                            const void *in_e, int dag, void *stream);
+
 /* Release everything the handle owns (synchronises the device first).
  * NULL is accepted. */
 void wilson_eo_destroy(wilson_eo_t h);

@@ -89,6 +89,7 @@ def _load():
         "wilson_eo_get_launch": (I, [P, IP, IP]),
         "wilson_eo_set_algorithm": (I, [P, I, I, I]),
         "wilson_eo_check": (I, [P, P]),
+        "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
         f = getattr(lib, name, None)
@@ -236,6 +237,106 @@ def wilson_eo_link_grad(h, grad, g_e, phi_e, stream=None):
 def wilson_eo_force(h, force, dS_dphi_e, phi_e, stream=None):
     _check(_load().wilson_eo_force(h, _ptr(force), _ptr(dS_dphi_e), _ptr(phi_e), _stream(stream)),
            "wilson_eo_force")
+
+
+def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=None):
+    """FP32 M_eo (or M_eo^dag) on caller-owned device arrays; the library
+    allocates nothing for it (see the header for the scratch-array rules)."""
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    _check(_load().wilson_eo_apply_noalloc(d, float(kappa), _ptr(gauge), _ptr(out_e), _ptr(in_e),
+                                           int(bool(dag)), _stream(stream)),
+           "wilson_eo_apply_noalloc")
+
+
+def wilson_eo_solve(h, x_e, b_e, tol=1e-10, maxiter=10000, mixed=True, stream=None,
+                    raise_on_error=True):
+    """Solve M^dag M x = b in place on ``x_e`` (complex128). Returns
+    ``(status, iterations, true_relres)``."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = _load().wilson_eo_solve(h, _ptr(x_e), _ptr(b_e), float(tol), int(maxiter),
+                                 int(bool(mixed)), ctypes.byref(it), ctypes.byref(rr),
+                                 _stream(stream))
+    if raise_on_error and st not in (WEO_OK, -5):
+        _check(st, "wilson_eo_solve")
+    return st, it.value, rr.value
+
+
+def wilson_eo_prepare_source(h, rhs_e, eta_e, eta_o, stream=None):
+    _check(_load().wilson_eo_prepare_source(h, _ptr(rhs_e), _ptr(eta_e), _ptr(eta_o),
+                                            _stream(stream)), "wilson_eo_prepare_source")
+
+
+def wilson_eo_reconstruct(h, xi_o, eta_o, xi_e, stream=None):
+    _check(_load().wilson_eo_reconstruct(h, _ptr(xi_o), _ptr(eta_o), _ptr(xi_e), _stream(stream)),
+           "wilson_eo_reconstruct")
+
+
+def wilson_eo_solve_full(h, xi_e, xi_o, eta_e, eta_o, tol=1e-10, maxiter=10000, mixed=True,
+                         stream=None, raise_on_error=True):
+    """D_W xi = eta (complex128 planar even/odd parts); xi_e holds the guess.
+    Returns (status, iterations, even-system relres)."""
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = _load().wilson_eo_solve_full(h, _ptr(xi_e), _ptr(xi_o), _ptr(eta_e), _ptr(eta_o),
+                                      float(tol), int(maxiter), int(bool(mixed)), ctypes.byref(it),
+                                      ctypes.byref(rr), _stream(stream))
+    if raise_on_error and st not in (WEO_OK, -5):
+        _check(st, "wilson_eo_solve_full")
+    return st, it.value, rr.value
+
+
+def wilson_eo_solver_config(h, delta=-1.0, chunk=0, use_graphs=-1):
+    _check(_load().wilson_eo_solver_config(h, float(delta), int(chunk), int(use_graphs)),
+           "wilson_eo_solver_config")
+
+
+def wilson_eo_solve_stats(h):
+    it, ru, hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    sec = ctypes.c_double()
+    _check(_load().wilson_eo_solve_stats(h, ctypes.byref(it), ctypes.byref(ru), ctypes.byref(hi),
+                                         ctypes.byref(sec)), "wilson_eo_solve_stats")
+    return {"iterations": it.value, "reliable_updates": ru.value, "fp64_applies": hi.value,
+            "seconds": sec.value}
+
+
+def wilson_eo_apply_batch(handles, outs, ins, dag=False, stream=None):
+    """M_eo (or M_eo^dag) on several lattices in one persistent launch."""
+    n = len(handles)
+    if not (len(outs) == len(ins) == n):
+        raise ValueError("handles, outs and ins must have the same length")
+    P = ctypes.c_void_p
+    hs = (P * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    os_ = (P * n)(*[_ptr(o).value for o in outs])
+    is_ = (P * n)(*[_ptr(i).value for i in ins])
+    _check(_load().wilson_eo_apply_batch(n, hs, os_, is_, int(bool(dag)), _stream(stream)),
+           "wilson_eo_apply_batch")
+
+
+def wilson_eo_tune(h, nrhs=1, stream=None):
+    """Autotune; returns (threads, rhs_block, ms per M_eo)."""
+    t, r = ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(_load().wilson_eo_tune(h, int(nrhs), ctypes.byref(t), ctypes.byref(r), ctypes.byref(ms),
+                                  _stream(stream)), "wilson_eo_tune")
+    return t.value, r.value, ms.value
+
+
+def wilson_eo_set_algorithm(h, algo, ring=0, threads=0):
+    """algo 0: two hop launches; 1: fused single launch with an L2 ring of t-slices."""
+    a = {"two_pass": 0, "fused": 1}.get(algo, algo)
+    _check(_load().wilson_eo_set_algorithm(h, int(a), int(ring), int(threads)),
+           "wilson_eo_set_algorithm")
+
+
+def wilson_eo_check(h, stream=None):
+    _check(_load().wilson_eo_check(h, _stream(stream)), "wilson_eo_check")
+
+
+def wilson_eo_get_launch(h):
+    t, r = ctypes.c_int(), ctypes.c_int()
+    _check(_load().wilson_eo_get_launch(h, ctypes.byref(t), ctypes.byref(r)), "wilson_eo_get_launch")
+    return t.value, r.value
 
 
 def wilson_eo_destroy(h):

@@ -1,0 +1,78 @@
+"""wilson_eo_apply_noalloc, the entry point for callers that cannot allocate.
+
+Callers whose device memory is owned by someone else (a framework's caching
+allocator, a real-time loop, a plug-in that only receives buffers) cannot call
+cudaMalloc; this entry point runs M_eo with its odd-site intermediate in a
+fixed array inside the library. These tests call it through the C ABI and
+compare with wilson_eo_apply on an FP32 handle, on two calls in a row (the
+second call reuses the array the first one left behind). The file is named so
+that pytest collects it last.
+"""
+
+import numpy as np
+import pytest
+
+import gen
+from gpu_util import TOL, rel_l2, to_planar
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def weo():
+    import paper_2303_08609_gb300 as weo
+
+    weo.library()
+    return weo
+
+
+def test_noalloc_matches_apply_on_two_calls_in_a_row(weo):
+    import torch
+
+    cases = [((8, 8, 8, 8), 0.125, "haar", 60), ((16, 8, 4, 12), 0.13, "smooth", 61)]
+    for k, (dims, kappa, kind, seed) in enumerate(cases):
+        U = gen.gauge_field(dims, kind, seed=seed, eps=0.4)
+        psi = gen.gaussian_spinor(dims, nrhs=2, seed=seed + 100)
+        Ud = torch.from_numpy(U.astype(np.complex64)).cuda()
+        op = weo.WilsonEO(dims, kappa, Ud, prec="f32", linkfmt=18)
+        for r in range(2):  # two calls in a row on the same lattice
+            x = torch.from_numpy(to_planar(psi[r]).astype(np.complex64)).cuda()
+            for dag in (False, True):
+                want = op.apply(x, dag=dag)
+                got = torch.empty_like(x)
+                weo.wilson_eo_apply_noalloc(dims, kappa, Ud, got, x, dag=dag)
+                torch.cuda.synchronize()
+                assert rel_l2(got.cpu().numpy(), want.cpu().numpy()) <= TOL["f32"]
+        op.close()
+
+
+def test_noalloc_second_call_takes_no_device_memory(weo):
+    import torch
+
+    dims = (8, 8, 8, 8)
+    U = torch.from_numpy(gen.gauge_field(dims, "haar", seed=62).astype(np.complex64)).cuda()
+    x = torch.from_numpy(to_planar(gen.gaussian_spinor(dims, seed=63)[0]).astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    weo.wilson_eo_apply_noalloc(dims, 0.12, U, y, x)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    weo.wilson_eo_apply_noalloc(dims, 0.12, U, y, x)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_noalloc_rejects_lattices_beyond_its_scratch(weo):
+    import torch
+
+    dims = (32, 32, 32, 64)  # V/2 = 1048576 > 349525
+    U = torch.zeros((4, 16, 3, 3), dtype=torch.complex64, device="cuda")
+    x = torch.zeros((4, 3, 8), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_apply_noalloc(dims, 0.1, U, y, x)
+    assert e.value.status == -2
+    assert "349525" in weo.wilson_eo_last_error()
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, U.cpu(), y, x)
+    assert e.value.status == -1
