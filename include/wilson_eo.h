@@ -211,10 +211,12 @@ int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
 int wilson_eo_apply_batch(int n, const wilson_eo_t *hs, void *const *outs,
                           const void *const *ins, int dag, void *stream);
 
-/* Autotune the hopping-kernel launch configuration for M_eo on this handle
- * with nrhs right-hand sides: every candidate (threads 64/128/192/256 per CTA;
- * 1, 2 or 4 right-hand sides per thread for FP32 handles) is timed with CUDA
- * events on `stream` and the fastest is kept (wilson_eo_get_launch). Results
+/* Autotune M_eo on this handle with nrhs right-hand sides: every candidate is
+ * timed with CUDA events on `stream` and the fastest is kept -- the two-launch
+ * algorithm with threads 64/128/192/256 per CTA and 1, 2 or 4 right-hand sides
+ * per thread (FP32 handles), and for FP32 / 16-bit handles the fused algorithm
+ * with rings of 4, 8, 16 t-slices and 128 / 256 threads (wilson_eo_get_launch,
+ * wilson_eo_get_algorithm). threads_out / rhs_block_out describe the winner. Results
  * are cached per process by (GPU, extents, precision, link format, nrhs) and,
  * if the environment variable WILSON_EO_TUNE_CACHE names a file, appended to it
  * and read back by later processes. Allocates two temporary spinor fields.
@@ -237,6 +239,17 @@ int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out
  * WEO_ERR_UNSUPPORTED. */
 int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads);
 
+/* Failure-path test of the fused kernel: runs one fused M_eo in which the
+ * first-hop items never publish their completion (a flag that nothing sets) and
+ * the poll limit is short (~0.3 ms), so the second-hop items' bounded waits run
+ * out; the kernel records the error and every CTA returns. wilson_eo_check then
+ * reports WEO_ERR_TIMEOUT. out_e receives garbage. Nothing faults, traps or
+ * hangs; the context stays usable. FP32 / 16-bit handles, device arrays. */
+int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e, void *stream);
+
+/* Current algorithm (0 two launches, 1 fused), fused ring size and threads. */
+int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *ring, int *threads);
+
 /* Wait for `stream` and report whether any fused launch of this handle since
  * the previous check gave up a bounded wait (WEO_ERR_TIMEOUT: the outputs of
  * those calls are invalid); clears the record. WEO_OK otherwise. */
@@ -244,6 +257,19 @@ int wilson_eo_check(wilson_eo_t h, void *stream);
 
 /* Current launch configuration of the handle's hopping kernels. */
 int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block);
+
+/* The hopping term of wilson_eo_hop computed as on `ranks` sub-domains of the
+ * lattice split along t (ranks divides Lt), with every t-hop that crosses a
+ * sub-domain boundary -- the periodic wrap included, so ranks = 1 exchanges
+ * with itself, as the forced communication of the paper's benchmark (Sec. 4)
+ * -- passed through face buffers: pack (EO1: forward faces projected, backward
+ * faces projected and multiplied by U^dag, Secs. 3.5-3.6), one device copy per
+ * face and rank, bulk hops inside each sub-domain, and the boundary finish
+ * (EO2). The result equals wilson_eo_hop up to rounding; it exercises the data
+ * path a multi-GPU split would use. FP64 / FP32 handles, device arrays, one
+ * right-hand side. */
+int wilson_eo_hop_split(wilson_eo_t h, int ranks, int out_parity, int dag, void *out,
+                        const void *in, void *stream);
 
 /* Launch configuration of the hopping kernels for the handle's precision:
  * threads per block (32..256, a multiple of 32) and right-hand sides per

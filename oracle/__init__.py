@@ -45,12 +45,7 @@ def build(force: bool = False) -> str:
         return _LIB
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    build()
-    lib = ctypes.CDLL(_LIB)
+def _bind(lib):
     P = ctypes.c_void_p
     I = ctypes.c_int
     D = ctypes.c_double
@@ -73,6 +68,34 @@ def _load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    return lib
+
+
+class use_library:
+    """Context manager: route every oracle call through another build of
+    ``wilson_oracle.c`` (the tests use it to check that planted mistakes are
+    caught by the pins)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _bind(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = _bind(ctypes.CDLL(_LIB))
     _lib = lib
     return lib
 

@@ -89,6 +89,9 @@ def _load():
         "wilson_eo_get_launch": (I, [P, IP, IP]),
         "wilson_eo_set_algorithm": (I, [P, I, I, I]),
         "wilson_eo_check": (I, [P, P]),
+        "wilson_eo_hop_split": (I, [P, I, I, I, P, P, P]),
+        "wilson_eo_inject_fused_timeout": (I, [P, P, P, P]),
+        "wilson_eo_get_algorithm": (I, [P, IP, IP, IP]),
         "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
@@ -327,6 +330,25 @@ def wilson_eo_set_algorithm(h, algo, ring=0, threads=0):
     a = {"two_pass": 0, "fused": 1}.get(algo, algo)
     _check(_load().wilson_eo_set_algorithm(h, int(a), int(ring), int(threads)),
            "wilson_eo_set_algorithm")
+
+
+def wilson_eo_get_algorithm(h):
+    a, r, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_load().wilson_eo_get_algorithm(h, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t)),
+           "wilson_eo_get_algorithm")
+    return {"algo": a.value, "ring": r.value, "threads": t.value}
+
+
+def wilson_eo_hop_split(h, ranks, out_parity, dag, out, inp, stream=None):
+    """Hopping term with the lattice split along t into `ranks` sub-domains and
+    every crossing hop exchanged through face buffers (forced self-exchange)."""
+    _check(_load().wilson_eo_hop_split(h, int(ranks), int(out_parity), int(bool(dag)), _ptr(out),
+                                       _ptr(inp), _stream(stream)), "wilson_eo_hop_split")
+
+
+def wilson_eo_inject_fused_timeout(h, out_e, in_e, stream=None):
+    _check(_load().wilson_eo_inject_fused_timeout(h, _ptr(out_e), _ptr(in_e), _stream(stream)),
+           "wilson_eo_inject_fused_timeout")
 
 
 def wilson_eo_check(h, stream=None):

@@ -273,6 +273,22 @@ int wilson_eo_set_kappa(wilson_eo_t h, double kappa)
     return WEO_OK;
 }
 
+int wilson_eo_hop_split(wilson_eo_t h, int ranks, int out_parity, int dag, void *out,
+                        const void *in, void *stream)
+{
+    try {
+        if (!h || !out || !in) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (out == in) return set_error(WEO_ERR_ARG, "out must not alias in");
+        if (out_parity != 0 && out_parity != 1) return set_error(WEO_ERR_ARG, "out_parity must be 0 or 1");
+        if (!is_device_pointer(out) || !is_device_pointer(in))
+            return set_error(WEO_ERR_ARG, "wilson_eo_hop_split takes device arrays");
+        DeviceGuard dg(h->device);
+        return hop_split_device(h, ranks, out_parity, dag != 0, out, in, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_hop_split");
+    }
+}
+
 int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved)
 {
     (void)reserved;
@@ -302,6 +318,20 @@ int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads)
     if (ring) h->fused_ring = ring;
     if (threads) h->fused_threads = threads;
     return WEO_OK;
+}
+
+int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e, void *stream)
+{
+    try {
+        if (!h || !out_e || !in_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (h->prec == WEO_F64) return set_error(WEO_ERR_UNSUPPORTED, "the fused M_eo has FP32 arithmetic only");
+        if (!is_device_pointer(out_e) || !is_device_pointer(in_e))
+            return set_error(WEO_ERR_ARG, "device arrays only");
+        DeviceGuard dg(h->device);
+        return meo_fused(h, h->gauge, out_e, in_e, false, static_cast<cudaStream_t>(stream), true);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_fused_timeout");
+    }
 }
 
 int wilson_eo_check(wilson_eo_t h, void *stream)
@@ -566,6 +596,7 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->stage_aux.release();
     h->fused_tmp.release();
     h->fused_ctrl.release();
+    h->halo.release();
     solver_destroy(h);
     prof_destroy(h);
     delete h;

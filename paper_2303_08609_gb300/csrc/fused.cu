@@ -47,6 +47,7 @@ struct FusedParams {
     unsigned int *ctrl;  // [0] sticky error (kept across launches), [1] ticket,
                          // [2] this launch's error, [3 .. 3+Lt) done A, [3+Lt .. 3+2Lt) done B
     unsigned int spin_limit;
+    int inject;      // test of the failure path: first-hop items never publish completion
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(THREADS) fused_meo_kernel(const FusedParams f)
             else fused_site<Lk, Dag, false>(f, t, s);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !(f.inject && !pb)) {
             __threadfence();
             atomicAdd(f.ctrl + 3 + (pb ? L : 0) + t, 1u);
         }
@@ -258,10 +259,25 @@ static int launch_fused_d(const FusedParams &f, bool dag, int threads, cudaStrea
     return dag ? launch_fused_t<Lk, true>(f, threads, s) : launch_fused_t<Lk, false>(f, threads, s);
 }
 
+// Size the ring and control words (outside any stream capture).
+int fused_prepare(wilson_eo_s *h, cudaStream_t s)
+{
+    const int L = h->dims[3];
+    const long long vs = (long long)(h->dims[0] / 2) * h->dims[1] * h->dims[2];
+    const int ring = std::max(3, h->fused_ring);
+    WEO_TRY(h->fused_tmp.ensure((size_t)(2 + ring) * 12 * vs * sizeof(float2)));
+    const size_t nctrl = (size_t)(3 + 2 * L);
+    if (!h->fused_ctrl.ptr || h->fused_ctrl.bytes < nctrl * sizeof(unsigned int)) {
+        WEO_TRY(h->fused_ctrl.ensure(nctrl * sizeof(unsigned int)));
+        WEO_CUDA(cudaMemsetAsync(h->fused_ctrl.ptr, 0, nctrl * sizeof(unsigned int), s));
+    }
+    return WEO_OK;
+}
+
 // M_eo (or M_eo^dag) with FP32 spinors through the fused kernel, links from `g`
 // (FP32, FP16 or BF16; 18 or 12 reals).
 int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, bool dag,
-              cudaStream_t s)
+              cudaStream_t s, bool inject_timeout)
 {
     if (g.prec == WEO_F64) return set_error(WEO_ERR_UNSUPPORTED, "the fused kernel has FP32 arithmetic only");
     const int L = h->dims[3];
@@ -274,12 +290,8 @@ int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, b
     f.vh = (int)h->vh;
     f.ring = std::max(3, h->fused_ring);
     const int threads = h->fused_threads == 256 ? 256 : 128;
-    WEO_TRY(h->fused_tmp.ensure((size_t)(2 + f.ring) * 12 * f.vs * sizeof(float2)));
+    WEO_TRY(fused_prepare(h, s));
     const size_t nctrl = (size_t)(3 + 2 * L);
-    if (!h->fused_ctrl.ptr || h->fused_ctrl.bytes < nctrl * sizeof(unsigned int)) {
-        WEO_TRY(h->fused_ctrl.ensure(nctrl * sizeof(unsigned int)));
-        WEO_CUDA(cudaMemsetAsync(h->fused_ctrl.ptr, 0, nctrl * sizeof(unsigned int), s));
-    }
     // reset the ticket, this launch's error and the completion counters
     WEO_CUDA(cudaMemsetAsync(static_cast<unsigned int *>(h->fused_ctrl.ptr) + 1, 0,
                              (nctrl - 1) * sizeof(unsigned int), s));
@@ -291,6 +303,8 @@ int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, b
     f.a = (float)(-h->kappa * h->kappa);
     f.ctrl = static_cast<unsigned int *>(h->fused_ctrl.ptr);
     f.spin_limit = 1u << 24;  // at least ~1 s of polling (64 ns sleeps) before giving up
+    f.inject = inject_timeout ? 1 : 0;
+    if (inject_timeout) f.spin_limit = 1u << 12;  // give up after ~0.3 ms
     f.chunks = f.total = 0;
     const bool c = g.fmt == WEO_LINK12;
     int tok = prof_begin(h, kernel_label("fused", g.prec, g.fmt, dag, true).c_str(), s);

@@ -29,6 +29,7 @@ namespace weo {
 
 constexpr int kRedBlocks = 1024;
 constexpr int kRedThreads = 256;
+constexpr int kMaxBreakdowns = 64;  // direction restarts before a solve gives up
 
 struct SolveScalars {
     double rr;       // |r|^2 of the iterated residual
@@ -111,6 +112,7 @@ template <typename T2>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, long long n,
                                                      SolveScalars *sc, int mode)
 {
+    if (mode == 1 && sc->nonfinite) return;  // the chunk stopped at a breakdown
     double v = 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x)
@@ -122,8 +124,9 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, l
             sc->red = tot;
         } else {
             sc->pAp = tot;
-            sc->alpha = sc->rr / tot;
-            if (!isfinite(tot) || !(tot > 0.0) || !isfinite(sc->alpha)) sc->nonfinite = 1;
+            const double alpha = sc->rr / tot;
+            if (!isfinite(tot) || !(tot > 0.0) || !isfinite(alpha)) sc->nonfinite = 1;
+            else sc->alpha = alpha;
         }
     }
 }
@@ -151,6 +154,7 @@ template <typename T2>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T2 *p, const T2 *Ap,
                                                            long long n, SolveScalars *sc)
 {
+    if (sc->nonfinite) return;
     using T = decltype(T2().x);
     const T alpha = T(sc->alpha);
     double v = 0.0;
@@ -169,9 +173,12 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
     v = block_sum(v);
     double tot;
     if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
-        sc->beta = tot / sc->rr;
-        sc->rr = tot;
-        if (!isfinite(tot) || !isfinite(sc->beta)) sc->nonfinite = 1;
+        if (!isfinite(tot) || !isfinite(tot / sc->rr)) {
+            sc->nonfinite = 1;
+        } else {
+            sc->beta = tot / sc->rr;
+            sc->rr = tot;
+        }
     }
 }
 
@@ -179,6 +186,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
 template <typename T2>
 __global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *sc)
 {
+    if (sc->nonfinite) return;
     using T = decltype(T2().x);
     const T beta = T(sc->beta);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
@@ -284,6 +292,16 @@ static int read_scalars(SolverState *S)
     WEO_CUDA(cudaMemcpyAsync(S->host, S->scal.ptr, offsetof(SolveScalars, counter), cudaMemcpyDeviceToHost,
                              S->stream));
     WEO_CUDA(cudaStreamSynchronize(S->stream));
+    return WEO_OK;
+}
+
+// After a chunk of fused-operator iterations: did a bounded wait give up?
+static int check_fused(wilson_eo_s *h, SolverState *S)
+{
+    if (h->algo != 1) return WEO_OK;
+    unsigned int err = 0;
+    WEO_TRY(fused_take_error(h, S->stream, &err));
+    if (err) return set_error(WEO_ERR_TIMEOUT, "a bounded wait in the fused M_eo kernel gave up during the solve");
     return WEO_OK;
 }
 
@@ -450,17 +468,27 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         WEO_CUDA(cudaGetLastError());
         double rr = rr_true;
         if (rr <= target) status = WEO_OK;
+        int breakdowns = 0;
         while (status != WEO_OK && S->iterations < maxiter) {
             const int k = std::min(S->chunk, maxiter - S->iterations);
             WEO_TRY(cg_chunk(h, S, *ghi, false, k));
             S->iterations += k;
             WEO_TRY(read_scalars(S));
-            if (S->host->nonfinite) return set_error(WEO_ERR_NONFINITE, "non-finite value in FP64 CG");
+            bool restart = false;
+            if (S->host->nonfinite) {
+                // <p, A p> <= 0 or a non-finite scalar: the chunk stopped updating
+                // at the last good iterate; restart from the recomputed residual
+                if (++breakdowns > kMaxBreakdowns)
+                    return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in FP64 CG");
+                WEO_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
+                restart = true;
+            }
             rr = S->host->rr;
-            if (rr <= target) {
+            if (rr <= target || restart) {
                 // confirm on the recomputed residual; restart from it if not met
                 WEO_TRY(true_residual(h, S, *ghi));
                 rr_true = S->host->red;
+                if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
                 if (rr_true <= target) {
                     status = WEO_OK;
                     break;
@@ -484,15 +512,26 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         WEO_CUDA(cudaGetLastError());
         double r_max = sqrt(rr_true);
         if (rr_true <= target) status = WEO_OK;
+        int breakdowns = 0;
         while (status != WEO_OK && S->iterations < maxiter) {
             const int k = std::min(S->chunk, maxiter - S->iterations);
             WEO_TRY(cg_chunk(h, S, *glo, true, k));
             S->iterations += k;
             WEO_TRY(read_scalars(S));
-            if (S->host->nonfinite)
-                return set_error(WEO_ERR_NONFINITE, "non-finite value in the low-precision CG");
+            WEO_TRY(check_fused(h, S));
+            bool restart = false;
+            if (S->host->nonfinite) {
+                // breakdown of the low-precision iteration (its operator is only
+                // approximately Hermitian positive): the chunk stopped at the last
+                // good iterate; reliable update and restart the direction
+                if (++breakdowns > kMaxBreakdowns)
+                    return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in the low-precision CG");
+                WEO_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
+                restart = true;
+            }
             const double rr = S->host->rr;
-            const bool update = sqrt(rr) < S->delta * r_max || rr <= target || S->iterations >= maxiter;
+            const bool update = restart || sqrt(rr) < S->delta * r_max || rr <= target ||
+                                S->iterations >= maxiter;
             if (!update) continue;
             // reliable update: fold the increment into x and recompute r in FP64
             k_accumulate<<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (float2 *)S->xs.ptr, n);
@@ -507,6 +546,8 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
             }
             r_max = sqrt(rr_true);
             k_convert<float2, double2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, n);
+            if (restart)
+                WEO_CUDA(cudaMemcpyAsync(S->p.ptr, S->rs.ptr, b32, cudaMemcpyDeviceToDevice, s));
             k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->rs.ptr, n, sc, 1);
             WEO_CUDA(cudaGetLastError());
         }
@@ -549,6 +590,7 @@ int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b
     // every buffer an iteration touches exists before a graph is captured
     WEO_TRY(S->oddlo.ensure((size_t)h->vh * 96));
     WEO_TRY(S->odd64.ensure(b64));
+    if (h->algo == 1) WEO_TRY(fused_prepare(h, S->stream));
     // order after the caller's prior work, then run on the solver's own stream
     WEO_CUDA(cudaStreamSynchronize(user));
     cudaStream_t s = S->stream;

@@ -1,9 +1,11 @@
-// Autotuner for the hopping kernels: times M_eo with each candidate launch
-// configuration (threads per CTA; right-hand sides per thread for FP32
-// handles) on the handle's own lattice and keeps the fastest. Results are
-// cached per process, keyed by (GPU name, extents, precision, link format,
-// nrhs), and optionally in a text file named by the environment variable
-// WILSON_EO_TUNE_CACHE (one "key threads rhs_block ms" line per entry).
+// Autotuner for M_eo: times each candidate on the handle's own lattice and
+// keeps the fastest. Candidates: the two-launch algorithm with 64..256 threads
+// per CTA and (FP32 handles) 1, 2 or 4 right-hand sides per thread; and, for
+// FP32 / 16-bit handles, the fused single-launch algorithm with rings of 4, 8
+// or 16 t-slices and 128 or 256 threads per CTA. Results are cached per
+// process, keyed by (GPU name, extents, precision, link format, nrhs), and
+// optionally in a text file named by the environment variable
+// WILSON_EO_TUNE_CACHE (one "v2 key algo threads rhs_block ring ms" line each).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -19,7 +21,7 @@
 namespace weo {
 
 struct TuneEntry {
-    int threads, rhs_block;
+    int algo, threads, rhs_block, ring;
     double ms;
 };
 
@@ -53,10 +55,11 @@ static void load_tune_file()
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char key[400];
+    char tag[8], key[400];
     TuneEntry e;
-    while (fscanf(f, "%399s %d %d %lf", key, &e.threads, &e.rhs_block, &e.ms) == 4)
-        g_tune_cache[key] = e;
+    while (fscanf(f, "%7s %399s %d %d %d %d %lf", tag, key, &e.algo, &e.threads, &e.rhs_block,
+                  &e.ring, &e.ms) == 7)
+        if (strcmp(tag, "v2") == 0) g_tune_cache[key] = e;
     fclose(f);
 }
 
@@ -66,7 +69,7 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d %.6f\n", key.c_str(), e.threads, e.rhs_block, e.ms);
+    fprintf(f, "v2 %s %d %d %d %d %.6f\n", key.c_str(), e.algo, e.threads, e.rhs_block, e.ring, e.ms);
     fclose(f);
 }
 
@@ -79,11 +82,18 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         load_tune_file();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            h->cfg[h->prec].threads = it->second.threads;
-            h->cfg[h->prec].rhs_block = it->second.rhs_block;
-            if (threads_out) *threads_out = it->second.threads;
-            if (rhs_out) *rhs_out = it->second.rhs_block;
-            if (ms_out) *ms_out = it->second.ms;
+            const TuneEntry &e = it->second;
+            h->algo = e.algo;
+            if (e.algo == 1) {
+                h->fused_threads = e.threads;
+                h->fused_ring = e.ring;
+            } else {
+                h->cfg[h->prec].threads = e.threads;
+                h->cfg[h->prec].rhs_block = e.rhs_block;
+            }
+            if (threads_out) *threads_out = e.threads;
+            if (rhs_out) *rhs_out = e.rhs_block;
+            if (ms_out) *ms_out = e.ms;
             return WEO_OK;
         }
     }
@@ -106,41 +116,69 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         if (nrhs >= 4) rb.push_back(4);
     }
     const LaunchCfg saved = h->cfg[h->prec];
+    const int saved_algo = h->algo, saved_ring = h->fused_ring, saved_fthreads = h->fused_threads;
     Profiler *saved_prof = h->prof;
     h->prof = nullptr;
-    TuneEntry best = {saved.threads, saved.rhs_block, 1e30};
-    for (int threads : {64, 128, 192, 256}) {
-        for (int r : rb) {
-            h->cfg[h->prec].threads = threads;
-            h->cfg[h->prec].rhs_block = r;
-            bool ok = true;
-            for (int w = 0; w < 2 && ok; ++w) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
-            if (!ok) continue;
-            const int reps = 5;
-            cudaEventRecord(e0, s);
-            for (int k = 0; k < reps && ok; ++k) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
-            cudaEventRecord(e1, s);
-            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
-                (void)cudaGetLastError();
-                continue;
-            }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (ms < best.ms) best = {threads, r, ms};
+    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved_ring, 1e30};
+    struct Cand {
+        int algo, threads, rb, ring;
+    };
+    std::vector<Cand> cands;
+    for (int threads : {64, 128, 192, 256})
+        for (int r : rb) cands.push_back({0, threads, r, 0});
+    if (h->prec != WEO_F64)
+        for (int ring : {4, 8, 16})
+            for (int threads : {128, 256}) cands.push_back({1, threads, 1, ring});
+    for (const Cand &c : cands) {
+        h->algo = c.algo;
+        if (c.algo == 1) {
+            h->fused_threads = c.threads;
+            h->fused_ring = c.ring;
+        } else {
+            h->cfg[h->prec].threads = c.threads;
+            h->cfg[h->prec].rhs_block = c.rb;
         }
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
+        if (!ok) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        const int reps = 5;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < reps && ok; ++k) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
+        cudaEventRecord(e1, s);
+        if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (c.algo == 1) {
+            unsigned int err = 0;
+            if (fused_take_error(h, s, &err) != WEO_OK || err) continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best.ms) best = {c.algo, c.threads, c.rb, c.ring, ms};
     }
     h->prof = saved_prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     in.release();
     out.release();
-    if (best.ms >= 1e30) {
-        h->cfg[h->prec] = saved;
-        return set_error(WEO_ERR_CUDA, "no launch configuration ran");
+    h->cfg[h->prec] = saved;
+    h->algo = saved_algo;
+    h->fused_ring = saved_ring;
+    h->fused_threads = saved_fthreads;
+    if (best.ms >= 1e30) return set_error(WEO_ERR_CUDA, "no launch configuration ran");
+    h->algo = best.algo;
+    if (best.algo == 1) {
+        h->fused_threads = best.threads;
+        h->fused_ring = best.ring;
+    } else {
+        h->cfg[h->prec].threads = best.threads;
+        h->cfg[h->prec].rhs_block = best.rhs_block;
     }
-    h->cfg[h->prec].threads = best.threads;
-    h->cfg[h->prec].rhs_block = best.rhs_block;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;
@@ -177,5 +215,14 @@ extern "C" int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block)
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
     if (threads) *threads = h->cfg[h->prec].threads;
     if (rhs_block) *rhs_block = h->cfg[h->prec].rhs_block;
+    return WEO_OK;
+}
+
+extern "C" int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *ring, int *threads)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (algo) *algo = h->algo;
+    if (ring) *ring = h->fused_ring;
+    if (threads) *threads = h->fused_threads;
     return WEO_OK;
 }

@@ -98,6 +98,7 @@ struct wilson_eo_s {
     int fused_threads = 128;
     weo::Buffer fused_tmp;   // ring of odd-site t-slices
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
+    weo::Buffer halo;        // face buffers of the domain-decomposed hop
 };
 
 namespace weo {
@@ -135,8 +136,12 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
              int nrhs, bool dag, cudaStream_t s);
 // fused.cu: single-launch M_eo with FP32 spinors; error word of bounded waits
 int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, bool dag,
-              cudaStream_t s);
+              cudaStream_t s, bool inject_timeout = false);
 int fused_take_error(wilson_eo_s *h, cudaStream_t s, unsigned int *err);
+int fused_prepare(wilson_eo_s *h, cudaStream_t s);
+// halo.cu: hop with the lattice split along t and every crossing hop exchanged
+int hop_split_device(wilson_eo_s *h, int ranks, int out_parity, bool dag, void *out,
+                     const void *in, cudaStream_t s);
 // M_eo / M_eo^dag on device arrays in the handle's external format (api.cu)
 int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s);
 // link gradient (force = 0) or force TA(G U^dag) (force = 1), force.cu

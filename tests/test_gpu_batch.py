@@ -135,8 +135,15 @@ def test_autotuner_caches_and_keeps_results(weo):
     y0 = op.apply(x)
     threads, rb, ms = weo.wilson_eo_tune(op.handle, nrhs=4)
     assert threads in (64, 128, 192, 256) and rb in (1, 2, 4) and ms > 0
-    assert weo.wilson_eo_get_launch(op.handle) == (threads, rb)
-    assert torch.equal(op.apply(x), y0)
+    algo = weo.wilson_eo_get_algorithm(op.handle)
+    if algo["algo"] == 0:
+        assert weo.wilson_eo_get_launch(op.handle) == (threads, rb)
+        assert torch.equal(op.apply(x), y0)  # same arithmetic per site
+    else:
+        assert algo["threads"] == threads and algo["ring"] in (4, 8, 16)
+        y = op.apply(x)
+        weo.wilson_eo_check(op.handle)
+        assert rel_l2(y.cpu().numpy(), y0.cpu().numpy()) <= 1e-6
     op2 = weo.WilsonEO(dims, 0.13, U, prec="f32")
     t0 = time.perf_counter()
     assert weo.wilson_eo_tune(op2.handle, nrhs=4) == (threads, rb, ms)  # cache hit

@@ -98,3 +98,27 @@ def test_fused_rejected_for_fp64(weo):
         weo.wilson_eo_set_algorithm(op.handle, "fused")
     assert e.value.status == -3
     op.close()
+
+
+def test_fused_bounded_wait_reports_timeout_and_recovers(weo, oracle_lib):
+    """Failure detection without a fault: first-hop completions are never
+    published, the second hop's bounded waits run out, wilson_eo_check reports
+    WEO_ERR_TIMEOUT once, and the next fused apply on the same context is correct."""
+    import torch
+
+    dims = (8, 8, 8, 16)
+    U = gen.gauge_field(dims, "haar", seed=106)
+    psi = gen.gaussian_spinor(dims, seed=107)[0]
+    op = weo.WilsonEO(dims, 0.12, to_device(U), prec="f32")
+    weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
+    x = to_device(to_planar(psi), "f32")
+    y = torch.empty_like(x)
+    weo.wilson_eo_inject_fused_timeout(op.handle, y, x)
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_check(op.handle)
+    assert e.value.status == -7
+    weo.wilson_eo_check(op.handle)  # the record was cleared
+    y = op.apply(x)
+    weo.wilson_eo_check(op.handle)
+    assert rel_l2(from_planar(y.cpu().numpy()), oracle_lib.meo(U, 0.12, psi, dims)) <= TOL["f32"]
+    op.close()
