@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--linkfmt", type=int, default=18)
     ap.add_argument("--algo", type=int, default=0, help="0: two hop launches, 1: fused")
     ap.add_argument("--ring", type=int, default=8, help="t-slices in the fused kernel's L2 ring")
+    ap.add_argument("--threads", type=int, default=128, help="threads per CTA of the hop kernels")
+    ap.add_argument("--order", type=int, default=1,
+                    help="1: second hop walks the sites downward (reads the freshest part first)")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
@@ -221,6 +224,7 @@ def run_ours(args, rank, world, local):
                       linkfmt=args.linkfmt)
     if args.algo:
         weo.wilson_eo_set_algorithm(op.handle, "fused", args.ring, 128)
+    weo.wilson_eo_set_launch(op.handle, args.threads, 1, args.order)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -355,6 +359,8 @@ def run_ours(args, rank, world, local):
         del Ud
 
     extra = {} if args.no_extras else extras(U, psi, dev, stream)
+    if not args.no_solve:
+        extra["multi_rhs_solve_12"] = multi_solve_comparison(U, dev)
     solve = None if args.no_solve else solve_comparison(dev, tuple(args.solve_dims))
 
     cpu = None
@@ -374,6 +380,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA,
                        "links": f"exp(i*{EPS}*H), {args.linkfmt}-real", "prec": args.prec,
                        "flop_per_site_per_meo": FLOP_PER_SITE,
+                       "algo": "fused" if args.algo else "two hop launches",
+                       "threads": args.threads, "second_hop_order": "down" if args.order else "up",
                        "l2": "inputs larger than L2 (604 MB of links per hop pass)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -492,6 +500,43 @@ def extras(U, psi, dev, stream):
     for o in ops:
         o.close()
     return out
+
+
+def multi_solve_comparison(U, dev):
+    """12 spin-colour point sources at one even site on the benchmark lattice
+    (32^3 x 64, kappa = 0.13), solved together to true residual 1e-10:
+    FP16-storage mixed CG vs plain FP64 CG, both with all 12 systems in lockstep."""
+    import torch
+
+    import paper_2303_08609_gb300 as weo
+
+    V = int(np.prod(DIMS))
+    vh = V // 2
+    site = int(np.random.default_rng(3).integers(vh))
+    b = torch.zeros((12, 4, 3, vh), dtype=torch.complex128, device=dev)
+    for s_ in range(4):
+        for c in range(3):
+            b[3 * s_ + c, s_, c, site] = 1.0
+    Ud = torch.from_numpy(U).to(dev)
+    res = {"lattice": list(DIMS), "kappa": KAPPA, "nrhs": 12, "tol": 1e-10}
+    for name, prec, mixed, rb in (("mixed_f16", "f16", True, 4), ("mixed_f32", "f32", True, 4),
+                                  ("plain_f64", "f64", False, 1)):
+        op = weo.WilsonEO(DIMS, KAPPA, Ud, prec=prec)
+        if rb > 1:
+            weo.wilson_eo_set_launch(op.handle, 128, rb)
+        try:
+            x, info = op.solve(b, tol=1e-10, maxiter=20000, mixed=mixed)
+            res[name] = {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
+                         "reliable_updates": info["reliable_updates"],
+                         "max_true_relres": max(info["true_relres"]), "converged": info["converged"]}
+            del x
+        except weo.WilsonEOError as exc:
+            res[name] = {"error": str(exc)}
+        op.close()
+        torch.cuda.empty_cache()
+    if res["plain_f64"].get("converged") and res["mixed_f16"].get("converged"):
+        res["speedup_f16_vs_plain_f64"] = round(res["plain_f64"]["seconds"] / res["mixed_f16"]["seconds"], 2)
+    return res
 
 
 def solve_comparison(dev, dims):

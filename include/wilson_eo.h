@@ -189,6 +189,18 @@ int wilson_eo_solve_full(wilson_eo_t h, void *xi_e, void *xi_o, const void *eta_
                          const void *eta_o, double tol, int maxiter, int mixed, int *iters_out,
                          double *relres_out, void *stream);
 
+/* wilson_eo_solve for nrhs (1..64) right-hand sides at once: x_e and b_e hold
+ * nrhs canonical complex128 even spinors. The systems run as independent CGs
+ * in lockstep -- every operator application covers all of them, so the
+ * multi-right-hand-side hop kernels read each link once for a block of
+ * right-hand sides -- each with its own scalars, convergence and restarts.
+ * iters_out[r] and true_relres_out[r] (arrays of nrhs, may be NULL) give the
+ * iteration at which system r met tol and its FP64 true residual. Status as in
+ * wilson_eo_solve; WEO_ERR_NOT_CONVERGED if any system missed tol. */
+int wilson_eo_solve_multi(wilson_eo_t h, void *x_e, const void *b_e, int nrhs, double tol,
+                          int maxiter, int mixed, int *iters_out, double *true_relres_out,
+                          void *stream);
+
 /* Solver settings: reliable-update threshold delta in (0, 1), iterations per
  * chunk (>= 1; default 8), use_graphs 1/0 (default 1). A value outside its range
  * leaves that setting unchanged. */
@@ -273,10 +285,13 @@ int wilson_eo_hop_split(wilson_eo_t h, int ranks, int out_parity, int dag, void 
 
 /* Launch configuration of the hopping kernels for the handle's precision:
  * threads per block (32..256, a multiple of 32) and right-hand sides per
- * thread (1, 2 or 4; values other than 1 apply to FP32 handles only, where the
+ * thread (1, 2 or 4; values other than 1 apply to FP32 and 16-bit handles, where the
  * links loaded for a site are shared by that many right-hand sides).
- * wilson_eo_tune (when present) sets these from measurements. */
-int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved);
+ * order 1 (default): the second hop of M_eo walks the sites from the top down,
+ * so it first reads the part of the odd intermediate the first hop wrote last,
+ * while that part is still in L2; order 0: both hops walk upward.
+ * wilson_eo_tune sets threads and rhs_block from measurements. */
+int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order);
 
 /* Per-kernel timing. With profiling on, every kernel the handle launches is
  * bracketed by two CUDA events on its stream (a few microseconds of host time

@@ -79,6 +79,7 @@ def _load():
         "wilson_eo_link_grad": (I, [P, P, P, P, P]),
         "wilson_eo_solve": (I, [P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
         "wilson_eo_solver_config": (I, [P, D, I, I]),
+        "wilson_eo_solve_multi": (I, [P, P, P, I, D, I, I, IP, ctypes.POINTER(D), P]),
         "wilson_eo_prepare_source": (I, [P, P, P, P, P]),
         "wilson_eo_reconstruct": (I, [P, P, P, P, P]),
         "wilson_eo_solve_full": (I, [P, P, P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
@@ -207,8 +208,9 @@ def wilson_eo_hop(h, out_parity, dag, out, inp, nrhs=1, stream=None):
                                  int(nrhs), _stream(stream)), "wilson_eo_hop")
 
 
-def wilson_eo_set_launch(h, threads, rhs_block=1):
-    _check(_load().wilson_eo_set_launch(h, int(threads), int(rhs_block), 0), "wilson_eo_set_launch")
+def wilson_eo_set_launch(h, threads, rhs_block=1, order=1):
+    _check(_load().wilson_eo_set_launch(h, int(threads), int(rhs_block), int(order)),
+           "wilson_eo_set_launch")
 
 
 def wilson_eo_profile(h, enable=True):
@@ -287,6 +289,19 @@ def wilson_eo_solve_full(h, xi_e, xi_o, eta_e, eta_o, tol=1e-10, maxiter=10000, 
     if raise_on_error and st not in (WEO_OK, -5):
         _check(st, "wilson_eo_solve_full")
     return st, it.value, rr.value
+
+
+def wilson_eo_solve_multi(h, x_e, b_e, nrhs, tol=1e-10, maxiter=10000, mixed=True, stream=None,
+                          raise_on_error=True):
+    """Solve nrhs systems M^dag M x_r = b_r in lockstep (complex128 planar, in place
+    on ``x_e``). Returns ``(status, iterations[nrhs], true_relres[nrhs])``."""
+    it = (ctypes.c_int * nrhs)()
+    rr = (ctypes.c_double * nrhs)()
+    st = _load().wilson_eo_solve_multi(h, _ptr(x_e), _ptr(b_e), int(nrhs), float(tol), int(maxiter),
+                                       int(bool(mixed)), it, rr, _stream(stream))
+    if raise_on_error and st not in (WEO_OK, -5):
+        _check(st, "wilson_eo_solve_multi")
+    return st, list(it), list(rr)
 
 
 def wilson_eo_solver_config(h, delta=-1.0, chunk=0, use_graphs=-1):
@@ -467,13 +482,19 @@ class WilsonEO:
         return F, d
 
     def solve(self, b, x0=None, tol=1e-10, maxiter=10000, mixed=True, stream=None):
-        """x with M^dag M x = b (complex128 planar). Returns (x, info dict)."""
+        """x with M^dag M x = b (complex128 planar; a leading batch dimension
+        solves several systems in lockstep). Returns (x, info dict)."""
         import torch
 
         x = torch.zeros_like(b) if x0 is None else x0.clone()
-        st, it, rr = wilson_eo_solve(self._h, x, b, tol, maxiter, mixed, stream)
+        if b.dim() == 3:
+            st, it, rr = wilson_eo_solve(self._h, x, b, tol, maxiter, mixed, stream)
+        else:
+            nrhs = int(np.prod(b.shape[:-3]))
+            st, it, rr = wilson_eo_solve_multi(self._h, x, b, nrhs, tol, maxiter, mixed, stream)
         info = wilson_eo_solve_stats(self._h)
-        info.update({"status": STATUS.get(st, st), "true_relres": rr, "converged": st == WEO_OK})
+        info.update({"status": STATUS.get(st, st), "true_relres": rr, "rhs_iterations": it,
+                     "converged": st == WEO_OK})
         return x, info
 
     def set_gauge(self, gauge, stream=None):

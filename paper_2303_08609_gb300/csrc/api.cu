@@ -169,6 +169,7 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
         p.x = in;
         p.x_stride = ext;
         p.a = -h->kappa * h->kappa;
+        p.reverse = h->alternate;  // read the intermediate's most recent part first
         return handle_hop(h, prec, g.fmt, IO_SAME, dag, true, p, s);
     }
     const long long s16 = h->vh * spinor_site_bytes(SK_H16);
@@ -187,6 +188,7 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
     p.x = in;
     p.x_stride = ext;
     p.a = -h->kappa * h->kappa;
+    p.reverse = h->alternate;
     return handle_hop(h, prec, g.fmt, IO_FROM16, dag, true, p, s);
 }
 
@@ -289,19 +291,20 @@ int wilson_eo_hop_split(wilson_eo_t h, int ranks, int out_parity, int dag, void 
     }
 }
 
-int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int reserved)
+int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order)
 {
-    (void)reserved;
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (order != 0 && order != 1) return set_error(WEO_ERR_ARG, "order must be 0 or 1");
     if (threads < 32 || threads > 1024 || threads % 32)
         return set_error(WEO_ERR_ARG, "threads must be a multiple of 32 in [32, 1024]");
     if (rhs_block != 1 && rhs_block != 2 && rhs_block != 4)
         return set_error(WEO_ERR_ARG, "rhs_block must be 1, 2 or 4");
-    if (rhs_block != 1 && h->prec != WEO_F32)
-        return set_error(WEO_ERR_UNSUPPORTED, "rhs_block > 1 needs an FP32 handle");
+    if (rhs_block != 1 && h->prec == WEO_F64)
+        return set_error(WEO_ERR_UNSUPPORTED, "rhs_block > 1 needs an FP32 or 16-bit handle");
     if (threads > 256) return set_error(WEO_ERR_UNSUPPORTED, "hopping kernels are built for <= 256 threads");
     h->cfg[h->prec].threads = threads;
     h->cfg[h->prec].rhs_block = rhs_block;
+    h->alternate = order;
     return WEO_OK;
 }
 
@@ -487,10 +490,33 @@ int wilson_eo_solve(wilson_eo_t h, void *x_e, const void *b_e, double tol, int m
         if (maxiter < 0) return set_error(WEO_ERR_ARG, "maxiter must be >= 0");
         DeviceGuard dg(h->device);
         const bool xh = !is_device_pointer(x_e), bh = !is_device_pointer(b_e);
-        return solve_device(h, x_e, b_e, xh, bh, tol, maxiter, mixed, iters_out, true_relres_out,
+        return solve_device(h, x_e, b_e, xh, bh, 1, tol, maxiter, mixed, iters_out, true_relres_out,
                             static_cast<cudaStream_t>(stream));
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solve");
+    }
+}
+
+int wilson_eo_solve_multi(wilson_eo_t h, void *x_e, const void *b_e, int nrhs, double tol,
+                          int maxiter, int mixed, int *iters_out, double *true_relres_out,
+                          void *stream)
+{
+    try {
+        if (!h || !x_e || !b_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (nrhs < 1 || nrhs > 64) return set_error(WEO_ERR_ARG, "nrhs must be in 1..64");
+        for (int r = 0; r < nrhs; ++r) {
+            if (iters_out) iters_out[r] = 0;
+            if (true_relres_out) true_relres_out[r] = -1.0;
+        }
+        if (x_e == b_e) return set_error(WEO_ERR_ARG, "x_e must not alias b_e");
+        if (!(tol > 0.0) || tol >= 1.0) return set_error(WEO_ERR_ARG, "tol must be in (0, 1)");
+        if (maxiter < 0) return set_error(WEO_ERR_ARG, "maxiter must be >= 0");
+        DeviceGuard dg(h->device);
+        const bool xh = !is_device_pointer(x_e), bh = !is_device_pointer(b_e);
+        return solve_device(h, x_e, b_e, xh, bh, nrhs, tol, maxiter, mixed, iters_out,
+                            true_relres_out, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solve_multi");
     }
 }
 

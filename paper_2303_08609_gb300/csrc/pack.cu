@@ -127,8 +127,8 @@ int launch_hop(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &
     switch (prec) {
     case WEO_F64: return launch_hop_f64(fmt, dag, axpy, p, cfg, s);
     case WEO_F32: return launch_hop_f32(fmt, dag, axpy, p, cfg, s);
-    case WEO_F16:
-    case WEO_BF16: return launch_hop_16(prec, fmt, io, dag, axpy, p, cfg, s);
+    case WEO_F16: return launch_hop_h16(fmt, io, dag, axpy, p, cfg, s);
+    case WEO_BF16: return launch_hop_b16(fmt, io, dag, axpy, p, cfg, s);
     default: return set_error(WEO_ERR_ARG, "unknown precision");
     }
 }

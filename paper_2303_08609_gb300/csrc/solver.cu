@@ -1,6 +1,6 @@
 // Solvers for M_eo^dag M_eo x = b (the normal equations of Eq. 4's even system;
 // the paper's Sec. 2 notes that the solver's speed is set by the matrix
-// multiplication).
+// multiplication), for one or several right-hand sides at once.
 //
 //  * plain FP64 conjugate gradient: every vector, operator and reduction in FP64;
 //  * mixed precision: CG iterated with an FP32 or 16-bit-storage operator and
@@ -12,24 +12,34 @@
 //    operator. The search direction is kept. Convergence is declared on that
 //    FP64 true residual only.
 //
+// Several right-hand sides run as independent CGs in lockstep: every operator
+// application covers all of them (the multi-RHS hop kernels read each link once
+// for a block of right-hand sides), every BLAS-1 kernel and reduction is a 2-D
+// grid over (elements, right-hand side), and each right-hand side has its own
+// scalars, convergence flag and restarts.
+//
 // All scalars (rho, alpha, beta) live on the device: the last block of each
 // reduction finishes it and derives the next scalar, so an iteration is a fixed
 // sequence of kernel launches with no host round trip. Iterations run in chunks
-// captured once as a CUDA graph and replayed; the host reads the residual norm
+// captured once as a CUDA graph and replayed; the host reads the residual norms
 // only between chunks. Reductions are deterministic (fixed grid, partial sums
 // added in block order).
 #include <math.h>
+#include <stddef.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
+#include <vector>
 
 #include "weo_internal.h"
 
 namespace weo {
 
-constexpr int kRedBlocks = 1024;
+constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
 constexpr int kMaxBreakdowns = 64;  // direction restarts before a solve gives up
+constexpr int kMaxRhs = 64;
 
 struct SolveScalars {
     double rr;       // |r|^2 of the iterated residual
@@ -38,28 +48,35 @@ struct SolveScalars {
     double beta;
     double red;      // result of the last plain reduction
     int nonfinite;   // set when a reduction or a scalar is NaN / Inf or pAp <= 0
+    int active;      // 0 once this right-hand side has converged
     unsigned int counter;
+    unsigned int pad;
     double partial[kRedBlocks];
 };
+constexpr size_t kHead = offsetof(SolveScalars, counter);
 
 struct SolverState {
-    Buffer scal;                 // SolveScalars on the device
-    SolveScalars *host = nullptr;  // pinned mirror of the leading scalars
+    Buffer scal;                     // nrhs x SolveScalars on the device
+    SolveScalars *host = nullptr;    // pinned mirror of the heads (kMaxRhs entries)
     Buffer x64, b64, r64, e64, t64, odd64;     // FP64 work vectors
     Buffer xs, rs, p, Ap, t32, oddlo;          // low-precision work vectors
     Buffer p64, Ap64;                          // plain FP64 CG
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [mixed]
     int graph_chunk[2] = {0, 0};
+    int graph_nrhs[2] = {0, 0};
     double delta = 0.1;
     int chunk = 8;
     int use_graphs = 1;
+    int nrhs = 1;                    // right-hand sides of the current solve
     // statistics of the last solve
     int iterations = 0, reliable_updates = 0, hi_applies = 0;
     double seconds = 0.0;
 };
 
 // ---------------------------------------------------------------- kernels --
+// Every kernel is a 2-D grid: blockIdx.y selects the right-hand side, whose
+// vectors start at offset rhs * n and whose scalars are sc[rhs].
 
 __device__ __forceinline__ double block_sum(double v)
 {
@@ -107,16 +124,20 @@ __device__ __forceinline__ bool finish_reduction(SolveScalars *sc, double block_
 template <typename T2>
 __device__ __forceinline__ double re_dot(T2 a, T2 b) { return double(a.x) * b.x + double(a.y) * b.y; }
 
-// mode 0: sc->red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp
+#define FOR_ELEMENTS(k) \
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+
+// mode 0: red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp
 template <typename T2>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, long long n,
-                                                     SolveScalars *sc, int mode)
+                                                     SolveScalars *scs, int mode)
 {
-    if (mode == 1 && sc->nonfinite) return;  // the chunk stopped at a breakdown
+    SolveScalars *sc = scs + blockIdx.y;
+    if (!sc->active || (mode == 1 && sc->nonfinite)) return;
+    a += blockIdx.y * n;
+    b += blockIdx.y * n;
     double v = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x)
-        v += re_dot(a[k], b[k]);
+    FOR_ELEMENTS(k) v += re_dot(a[k], b[k]);
     v = block_sum(v);
     double tot;
     if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
@@ -131,15 +152,16 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, l
     }
 }
 
-// mode 0: sc->red = |a|^2;  mode 1: sc->rr = |a|^2
+// mode 0: red = |a|^2 (every right-hand side);  mode 1: rr = |a|^2 (active ones)
 template <typename T2>
-__global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n, SolveScalars *sc,
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n, SolveScalars *scs,
                                                        int mode)
 {
+    SolveScalars *sc = scs + blockIdx.y;
+    if (mode == 1 && !sc->active) return;
+    a += blockIdx.y * n;
     double v = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x)
-        v += re_dot(a[k], a[k]);
+    FOR_ELEMENTS(k) v += re_dot(a[k], a[k]);
     v = block_sum(v);
     double tot;
     if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
@@ -152,14 +174,19 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n,
 // x += alpha p ; r -= alpha Ap ; rr_new = |r|^2 ; beta = rr_new / rr ; rr = rr_new
 template <typename T2>
 __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T2 *p, const T2 *Ap,
-                                                           long long n, SolveScalars *sc)
+                                                           long long n, SolveScalars *scs)
 {
-    if (sc->nonfinite) return;
+    SolveScalars *sc = scs + blockIdx.y;
+    if (!sc->active || sc->nonfinite) return;
     using T = decltype(T2().x);
+    const long long o = blockIdx.y * n;
+    x += o;
+    r += o;
+    p += o;
+    Ap += o;
     const T alpha = T(sc->alpha);
     double v = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    FOR_ELEMENTS(k) {
         T2 xv = x[k], rv = r[k];
         const T2 pv = p[k], av = Ap[k];
         xv.x += alpha * pv.x;
@@ -184,13 +211,16 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
 
 // p = r + beta p
 template <typename T2>
-__global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *sc)
+__global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *scs)
 {
-    if (sc->nonfinite) return;
+    const SolveScalars *sc = scs + blockIdx.y;
+    if (!sc->active || sc->nonfinite) return;
     using T = decltype(T2().x);
+    const long long o = blockIdx.y * n;
+    p += o;
+    r += o;
     const T beta = T(sc->beta);
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    FOR_ELEMENTS(k) {
         T2 pv = p[k];
         const T2 rv = r[k];
         pv.x = rv.x + beta * pv.x;
@@ -199,31 +229,32 @@ __global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *sc
     }
 }
 
-// r = b - t ; sc->red = |r|^2
+// r = b - t ; red = |r|^2 (every right-hand side)
 __global__ void __launch_bounds__(kRedThreads) k_residual(double2 *r, const double2 *b,
                                                           const double2 *t, long long n,
-                                                          SolveScalars *sc)
+                                                          SolveScalars *scs)
 {
+    SolveScalars *sc = scs + blockIdx.y;
+    const long long o = blockIdx.y * n;
+    r += o;
+    b += o;
+    t += o;
     double v = 0.0;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    FOR_ELEMENTS(k) {
         double2 rv = make_double2(b[k].x - t[k].x, b[k].y - t[k].y);
         r[k] = rv;
         v += rv.x * rv.x + rv.y * rv.y;
     }
     v = block_sum(v);
     double tot;
-    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
-        sc->red = tot;
-        if (!isfinite(tot)) sc->nonfinite = 1;
-    }
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) sc->red = tot;
 }
 
+// d = s over all right-hand sides (n_total elements)
 template <typename D2, typename S2>
 __global__ void k_convert(D2 *d, const S2 *s, long long n)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    FOR_ELEMENTS(k) {
         const S2 v = s[k];
         D2 o;
         o.x = v.x;
@@ -232,11 +263,10 @@ __global__ void k_convert(D2 *d, const S2 *s, long long n)
     }
 }
 
-// x64 += xs ; xs = 0
+// x64 += xs ; xs = 0 (n_total elements)
 __global__ void k_accumulate(double2 *x, float2 *xs, long long n)
 {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x) {
+    FOR_ELEMENTS(k) {
         const float2 v = xs[k];
         double2 a = x[k];
         a.x += v.x;
@@ -250,6 +280,12 @@ static unsigned red_grid(long long n)
 {
     long long b = (n + kRedThreads - 1) / kRedThreads;
     return (unsigned)(b < kRedBlocks ? (b < 1 ? 1 : b) : kRedBlocks);
+}
+
+static unsigned flat_grid(long long n)
+{
+    long long b = (n + 255) / 256;
+    return (unsigned)std::min<long long>(std::max<long long>(b, 1), 65535LL * 8);
 }
 
 // ------------------------------------------------------------------ state --
@@ -276,10 +312,10 @@ static int solver_state(wilson_eo_s *h, SolverState **out)
         h->solver = S;
         cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return fail_cuda(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
-        e = cudaMallocHost(&S->host, sizeof(SolveScalars));
+        e = cudaMallocHost(&S->host, sizeof(SolveScalars) * kMaxRhs);
         if (e != cudaSuccess) return fail_cuda(e, "cudaMallocHost", __FILE__, __LINE__);
-        WEO_TRY(S->scal.ensure(sizeof(SolveScalars)));
-        WEO_CUDA(cudaMemsetAsync(S->scal.ptr, 0, sizeof(SolveScalars), S->stream));
+        WEO_TRY(S->scal.ensure(sizeof(SolveScalars) * kMaxRhs));
+        WEO_CUDA(cudaMemsetAsync(S->scal.ptr, 0, sizeof(SolveScalars) * kMaxRhs, S->stream));
     }
     *out = h->solver;
     return WEO_OK;
@@ -287,11 +323,21 @@ static int solver_state(wilson_eo_s *h, SolverState **out)
 
 static SolveScalars *dev_scal(SolverState *S) { return static_cast<SolveScalars *>(S->scal.ptr); }
 
+// heads of every right-hand side's scalars into S->host (blocking)
 static int read_scalars(SolverState *S)
 {
-    WEO_CUDA(cudaMemcpyAsync(S->host, S->scal.ptr, offsetof(SolveScalars, counter), cudaMemcpyDeviceToHost,
-                             S->stream));
+    WEO_CUDA(cudaMemcpy2DAsync(S->host, sizeof(SolveScalars), S->scal.ptr, sizeof(SolveScalars), kHead,
+                               S->nrhs, cudaMemcpyDeviceToHost, S->stream));
     WEO_CUDA(cudaStreamSynchronize(S->stream));
+    return WEO_OK;
+}
+
+static int set_flag(SolverState *S, int rhs, size_t offset, int value)
+{
+    // a tiny host-to-device write of one int field of sc[rhs]
+    char *dst = static_cast<char *>(S->scal.ptr) + rhs * sizeof(SolveScalars) + offset;
+    static const int vals[2] = {0, 1};
+    WEO_CUDA(cudaMemcpyAsync(dst, &vals[value ? 1 : 0], sizeof(int), cudaMemcpyHostToDevice, S->stream));
     return WEO_OK;
 }
 
@@ -331,30 +377,30 @@ static int lo_gauge(wilson_eo_s *h, const PackedGauge **g, cudaStream_t s)
     return WEO_OK;
 }
 
-// A v = M^dag (M v) with gauge g; e: even temporary, odd: odd temporary
-static int normal_op(wilson_eo_s *h, const PackedGauge &g, Buffer &odd, void *e, void *out,
-                     const void *v, cudaStream_t s)
+// A v = M^dag (M v) with gauge g for all right-hand sides
+static int normal_op(wilson_eo_s *h, SolverState *S, const PackedGauge &g, Buffer &odd, void *e,
+                     void *out, const void *v, cudaStream_t s)
 {
-    WEO_TRY(meo_with(h, g, odd, e, v, 1, false, s));
-    return meo_with(h, g, odd, out, e, 1, true, s);
+    WEO_TRY(meo_with(h, g, odd, e, v, S->nrhs, false, s));
+    return meo_with(h, g, odd, out, e, S->nrhs, true, s);
 }
 
-// One CG iteration. mixed: low-precision vectors (float2) with operator glo;
-// otherwise FP64 vectors with operator ghi.
+// One CG iteration of every right-hand side. mixed: low-precision vectors
+// (float2) with operator g; otherwise FP64 vectors.
 static int cg_iteration(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bool mixed,
                         cudaStream_t s)
 {
     const long long n = 12 * h->vh;
-    const unsigned grid = red_grid(n);
+    const dim3 grid(red_grid(n), S->nrhs);
     SolveScalars *sc = dev_scal(S);
     if (mixed) {
-        WEO_TRY(normal_op(h, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
+        WEO_TRY(normal_op(h, S, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
         k_dot<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc, 1);
         k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->rs.ptr,
                                                           (const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc);
         k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->p.ptr, (const float2 *)S->rs.ptr, n, sc);
     } else {
-        WEO_TRY(normal_op(h, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
+        WEO_TRY(normal_op(h, S, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
         k_dot<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc, 1);
         k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->r64.ptr,
                                                            (const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
@@ -373,7 +419,7 @@ static int cg_chunk(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bool m
         return WEO_OK;
     }
     const int gi = mixed ? 1 : 0;
-    if (!S->graph[gi] || S->graph_chunk[gi] != k) {
+    if (!S->graph[gi] || S->graph_chunk[gi] != k || S->graph_nrhs[gi] != S->nrhs) {
         if (S->graph[gi]) {
             cudaGraphExecDestroy(S->graph[gi]);
             S->graph[gi] = nullptr;
@@ -403,19 +449,21 @@ static int cg_chunk(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bool m
             return fail_cuda(e, "cudaGraphInstantiate", __FILE__, __LINE__);
         }
         S->graph_chunk[gi] = k;
+        S->graph_nrhs[gi] = S->nrhs;
     }
     WEO_CUDA(cudaGraphLaunch(S->graph[gi], s));
     return WEO_OK;
 }
 
-// r64 = b64 - A x64 with the FP64 operator; returns |r|^2 in S->host->red
+// r64 = b64 - A x64 with the FP64 operator for every right-hand side;
+// |r|^2 of each lands in S->host[rhs].red
 static int true_residual(wilson_eo_s *h, SolverState *S, const PackedGauge &ghi)
 {
     cudaStream_t s = S->stream;
     const long long n = 12 * h->vh;
-    WEO_TRY(normal_op(h, ghi, S->odd64, S->e64.ptr, S->t64.ptr, S->x64.ptr, s));
-    k_residual<<<red_grid(n), kRedThreads, 0, s>>>((double2 *)S->r64.ptr, (const double2 *)S->b64.ptr,
-                                                    (const double2 *)S->t64.ptr, n, dev_scal(S));
+    WEO_TRY(normal_op(h, S, ghi, S->odd64, S->e64.ptr, S->t64.ptr, S->x64.ptr, s));
+    k_residual<<<dim3(red_grid(n), S->nrhs), kRedThreads, 0, s>>>(
+        (double2 *)S->r64.ptr, (const double2 *)S->b64.ptr, (const double2 *)S->t64.ptr, n, dev_scal(S));
     WEO_CUDA(cudaGetLastError());
     S->hi_applies += 1;
     return read_scalars(S);
@@ -426,39 +474,53 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
 {
     SolverState *S = h->solver;
     cudaStream_t s = S->stream;
-    const long long n = 12 * h->vh;
-    const size_t b64 = (size_t)n * 16, b32 = (size_t)n * 8;
-    const unsigned grid = red_grid(n);
+    const int R = S->nrhs;
+    const long long n = 12 * h->vh, nt = n * R;
+    const size_t b64 = (size_t)nt * 16, b32 = (size_t)nt * 8, v64 = (size_t)n * 16, v32 = (size_t)n * 8;
+    const dim3 grid(red_grid(n), R);
     SolveScalars *sc = dev_scal(S);
     const PackedGauge *ghi = nullptr, *glo = nullptr;
     WEO_TRY(hi_gauge(h, &ghi, s));
     WEO_TRY(S->r64.ensure(b64));
     WEO_TRY(S->e64.ensure(b64));
     WEO_TRY(S->t64.ensure(b64));
-    WEO_TRY(S->odd64.ensure(b64));
-    WEO_CUDA(cudaMemsetAsync(sc, 0, offsetof(SolveScalars, partial), s));
+    // reset every right-hand side's scalars and mark them active
+    WEO_CUDA(cudaMemsetAsync(sc, 0, sizeof(SolveScalars) * R, s));
+    for (int r = 0; r < R; ++r) WEO_TRY(set_flag(S, r, offsetof(SolveScalars, active), 1));
     S->iterations = S->reliable_updates = S->hi_applies = 0;
+    std::vector<int> active(R, 1), iters(R, 0);
+    std::vector<double> target(R), rr_true(R), r_max(R);
 
-    // |b|^2
+    // |b|^2 of every right-hand side
     k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->b64.ptr, n, sc, 0);
     WEO_CUDA(cudaGetLastError());
     WEO_TRY(read_scalars(S));
-    const double bb = S->host->red;
-    if (!(bb > 0.0) || !isfinite(bb)) {
-        if (bb == 0.0) {  // b = 0: x = 0 is exact
-            WEO_CUDA(cudaMemsetAsync(S->x64.ptr, 0, b64, s));
-            if (iters_out) *iters_out = 0;
-            if (relres_out) *relres_out = 0.0;
-            return WEO_OK;
-        }
-        return set_error(WEO_ERR_NONFINITE, "non-finite right-hand side");
+    std::vector<double> bb(R);
+    for (int r = 0; r < R; ++r) {
+        bb[r] = S->host[r].red;
+        if (!isfinite(bb[r])) return set_error(WEO_ERR_NONFINITE, "non-finite right-hand side");
+        target[r] = tol * tol * bb[r];
     }
-    const double target = tol * tol * bb;
 
+    // b = 0: x = 0 is exact
+    for (int r = 0; r < R; ++r)
+        if (bb[r] == 0.0)
+            WEO_CUDA(cudaMemsetAsync(static_cast<char *>(S->x64.ptr) + r * v64, 0, v64, s));
     WEO_TRY(true_residual(h, S, *ghi));
-    double rr_true = S->host->red;
-    int status = WEO_ERR_NOT_CONVERGED;
-    if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite initial residual");
+    int n_active = R;
+    auto retire = [&](int r) -> int {  // right-hand side r has converged
+        active[r] = 0;
+        iters[r] = S->iterations;
+        --n_active;
+        return set_flag(S, r, offsetof(SolveScalars, active), 0);
+    };
+    for (int r = 0; r < R; ++r) {
+        rr_true[r] = S->host[r].red;
+        if (!isfinite(rr_true[r])) return set_error(WEO_ERR_NONFINITE, "non-finite initial residual");
+        r_max[r] = sqrt(rr_true[r]);
+        if (bb[r] == 0.0 || rr_true[r] <= target[r]) WEO_TRY(retire(r));
+    }
+    int breakdowns = 0;
 
     if (!mixed) {
         WEO_TRY(S->p64.ensure(b64));
@@ -466,37 +528,44 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         WEO_CUDA(cudaMemcpyAsync(S->p64.ptr, S->r64.ptr, b64, cudaMemcpyDeviceToDevice, s));
         k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->r64.ptr, n, sc, 1);
         WEO_CUDA(cudaGetLastError());
-        double rr = rr_true;
-        if (rr <= target) status = WEO_OK;
-        int breakdowns = 0;
-        while (status != WEO_OK && S->iterations < maxiter) {
+        while (n_active > 0 && S->iterations < maxiter) {
             const int k = std::min(S->chunk, maxiter - S->iterations);
             WEO_TRY(cg_chunk(h, S, *ghi, false, k));
             S->iterations += k;
             WEO_TRY(read_scalars(S));
-            bool restart = false;
-            if (S->host->nonfinite) {
-                // <p, A p> <= 0 or a non-finite scalar: the chunk stopped updating
-                // at the last good iterate; restart from the recomputed residual
-                if (++breakdowns > kMaxBreakdowns)
-                    return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in FP64 CG");
-                WEO_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
-                restart = true;
-            }
-            rr = S->host->rr;
-            if (rr <= target || restart) {
-                // confirm on the recomputed residual; restart from it if not met
-                WEO_TRY(true_residual(h, S, *ghi));
-                rr_true = S->host->red;
-                if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
-                if (rr_true <= target) {
-                    status = WEO_OK;
-                    break;
+            std::vector<int> restart(R, 0);
+            bool any = false;
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                if (S->host[r].nonfinite) {
+                    // <p, A p> <= 0 or a non-finite scalar: that system stopped
+                    // at its last good iterate; restart it from the true residual
+                    if (++breakdowns > kMaxBreakdowns)
+                        return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in FP64 CG");
+                    WEO_TRY(set_flag(S, r, offsetof(SolveScalars, nonfinite), 0));
+                    restart[r] = 1;
+                    any = true;
+                } else if (S->host[r].rr <= target[r]) {
+                    any = true;  // confirm on the recomputed residual
                 }
-                WEO_CUDA(cudaMemcpyAsync(S->p64.ptr, S->r64.ptr, b64, cudaMemcpyDeviceToDevice, s));
-                k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->r64.ptr, n, sc, 1);
-                WEO_CUDA(cudaGetLastError());
             }
+            if (!any) continue;
+            WEO_TRY(true_residual(h, S, *ghi));
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                rr_true[r] = S->host[r].red;
+                if (!isfinite(rr_true[r])) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
+                if (rr_true[r] <= target[r]) {
+                    WEO_TRY(retire(r));
+                } else if (restart[r] || S->host[r].rr <= target[r]) {
+                    WEO_CUDA(cudaMemcpyAsync(static_cast<char *>(S->p64.ptr) + r * v64,
+                                             static_cast<const char *>(S->r64.ptr) + r * v64, v64,
+                                             cudaMemcpyDeviceToDevice, s));
+                }
+            }
+            // iterated residual := recomputed one for the systems still running
+            k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->r64.ptr, n, sc, 1);
+            WEO_CUDA(cudaGetLastError());
         }
     } else {
         WEO_TRY(lo_gauge(h, &glo, s));
@@ -506,60 +575,73 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         WEO_TRY(S->Ap.ensure(b32));
         WEO_TRY(S->t32.ensure(b32));
         WEO_CUDA(cudaMemsetAsync(S->xs.ptr, 0, b32, s));
-        k_convert<float2, double2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, n);
+        k_convert<float2, double2><<<flat_grid(nt), 256, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, nt);
         WEO_CUDA(cudaMemcpyAsync(S->p.ptr, S->rs.ptr, b32, cudaMemcpyDeviceToDevice, s));
         k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->rs.ptr, n, sc, 1);
         WEO_CUDA(cudaGetLastError());
-        double r_max = sqrt(rr_true);
-        if (rr_true <= target) status = WEO_OK;
-        int breakdowns = 0;
-        while (status != WEO_OK && S->iterations < maxiter) {
+        while (n_active > 0 && S->iterations < maxiter) {
             const int k = std::min(S->chunk, maxiter - S->iterations);
             WEO_TRY(cg_chunk(h, S, *glo, true, k));
             S->iterations += k;
             WEO_TRY(read_scalars(S));
             WEO_TRY(check_fused(h, S));
-            bool restart = false;
-            if (S->host->nonfinite) {
-                // breakdown of the low-precision iteration (its operator is only
-                // approximately Hermitian positive): the chunk stopped at the last
-                // good iterate; reliable update and restart the direction
-                if (++breakdowns > kMaxBreakdowns)
-                    return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in the low-precision CG");
-                WEO_CUDA(cudaMemsetAsync(&sc->nonfinite, 0, sizeof(int), s));
-                restart = true;
+            std::vector<int> restart(R, 0);
+            bool update = S->iterations >= maxiter;
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                if (S->host[r].nonfinite) {
+                    // breakdown of the low-precision iteration (its operator is
+                    // only approximately Hermitian positive): reliable update and
+                    // restart that system's direction
+                    if (++breakdowns > kMaxBreakdowns)
+                        return set_error(WEO_ERR_NONFINITE, "repeated breakdown (non-finite or non-positive <p,Ap>) in the low-precision CG");
+                    WEO_TRY(set_flag(S, r, offsetof(SolveScalars, nonfinite), 0));
+                    restart[r] = 1;
+                    update = true;
+                }
+                const double rr = S->host[r].rr;
+                if (sqrt(rr) < S->delta * r_max[r] || rr <= target[r]) update = true;
             }
-            const double rr = S->host->rr;
-            const bool update = restart || sqrt(rr) < S->delta * r_max || rr <= target ||
-                                S->iterations >= maxiter;
             if (!update) continue;
-            // reliable update: fold the increment into x and recompute r in FP64
-            k_accumulate<<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (float2 *)S->xs.ptr, n);
+            // reliable update of every system: fold the increments into x and
+            // recompute the residuals in FP64
+            k_accumulate<<<flat_grid(nt), 256, 0, s>>>((double2 *)S->x64.ptr, (float2 *)S->xs.ptr, nt);
             WEO_CUDA(cudaGetLastError());
             WEO_TRY(true_residual(h, S, *ghi));
             S->reliable_updates += 1;
-            rr_true = S->host->red;
-            if (!isfinite(rr_true)) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
-            if (rr_true <= target) {
-                status = WEO_OK;
-                break;
+            for (int r = 0; r < R; ++r) {
+                if (!active[r]) continue;
+                rr_true[r] = S->host[r].red;
+                if (!isfinite(rr_true[r])) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
+                if (rr_true[r] <= target[r]) WEO_TRY(retire(r));
+                else r_max[r] = sqrt(rr_true[r]);
             }
-            r_max = sqrt(rr_true);
-            k_convert<float2, double2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, n);
-            if (restart)
-                WEO_CUDA(cudaMemcpyAsync(S->p.ptr, S->rs.ptr, b32, cudaMemcpyDeviceToDevice, s));
+            if (n_active == 0) break;
+            k_convert<float2, double2><<<flat_grid(nt), 256, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, nt);
+            for (int r = 0; r < R; ++r)
+                if (active[r] && restart[r])
+                    WEO_CUDA(cudaMemcpyAsync(static_cast<char *>(S->p.ptr) + r * v32,
+                                             static_cast<const char *>(S->rs.ptr) + r * v32, v32,
+                                             cudaMemcpyDeviceToDevice, s));
             k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->rs.ptr, n, sc, 1);
             WEO_CUDA(cudaGetLastError());
         }
     }
-    if (status != WEO_OK) {
-        // report the residual of the returned iterate
+    int status = WEO_OK;
+    if (n_active > 0) {
+        // report the residuals of the returned iterates
         WEO_TRY(true_residual(h, S, *ghi));
-        rr_true = S->host->red;
-        set_error(WEO_ERR_NOT_CONVERGED, "maxiter reached before the true residual met tol");
+        for (int r = 0; r < R; ++r)
+            if (active[r]) {
+                rr_true[r] = S->host[r].red;
+                iters[r] = S->iterations;
+            }
+        status = set_error(WEO_ERR_NOT_CONVERGED, "maxiter reached before every true residual met tol");
     }
-    if (iters_out) *iters_out = S->iterations;
-    if (relres_out) *relres_out = sqrt(rr_true / bb);
+    for (int r = 0; r < R; ++r) {
+        if (iters_out) iters_out[r] = iters[r];
+        if (relres_out) relres_out[r] = bb[r] > 0.0 ? sqrt(rr_true[r] / bb[r]) : 0.0;
+    }
     return status;
 }
 
@@ -578,17 +660,19 @@ int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs)
     return WEO_OK;
 }
 
-int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host,
+int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host, int nrhs,
                  double tol, int maxiter, int mixed, int *iters_out, double *relres_out,
                  cudaStream_t user)
 {
+    if (nrhs < 1 || nrhs > kMaxRhs) return set_error(WEO_ERR_ARG, "nrhs must be in 1..64");
     SolverState *S;
     WEO_TRY(solver_state(h, &S));
-    const size_t b64 = (size_t)12 * h->vh * 16;
+    S->nrhs = nrhs;
+    const size_t b64 = (size_t)12 * h->vh * 16 * nrhs;
     WEO_TRY(S->x64.ensure(b64));
     WEO_TRY(S->b64.ensure(b64));
     // every buffer an iteration touches exists before a graph is captured
-    WEO_TRY(S->oddlo.ensure((size_t)h->vh * 96));
+    WEO_TRY(S->oddlo.ensure((size_t)h->vh * 96 * nrhs));
     WEO_TRY(S->odd64.ensure(b64));
     if (h->algo == 1) WEO_TRY(fused_prepare(h, S->stream));
     // order after the caller's prior work, then run on the solver's own stream
@@ -695,7 +779,7 @@ int solve_full_device(wilson_eo_s *h, void *xi_e, void *xi_o, const void *eta_e,
         cleanup();
         return fail_cuda(cudaGetLastError(), "cudaMemcpyAsync", __FILE__, __LINE__);
     }
-    st = solve_device(h, rhs.ptr, ee.ptr, false, false, tol, maxiter, mixed, iters_out, relres_out, s);
+    st = solve_device(h, rhs.ptr, ee.ptr, false, false, 1, tol, maxiter, mixed, iters_out, relres_out, s);
     if (st != WEO_OK && st != WEO_ERR_NOT_CONVERGED) { cleanup(); return st; }
     const int solve_status = st;
     // xi_o = eta_o + kappa H_oe xi_e  (into ee)

@@ -111,7 +111,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     std::vector<int> rb = {1};
-    if (h->prec == WEO_F32) {
+    if (h->prec != WEO_F64) {
         if (nrhs >= 2) rb.push_back(2);
         if (nrhs >= 4) rb.push_back(4);
     }

@@ -94,6 +94,7 @@ struct wilson_eo_s {
     weo::SolverState *solver = nullptr;
     // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
     int algo = 0;
+    int alternate = 1;       // second hop walks the sites in reverse order
     int fused_ring = 8;
     int fused_threads = 128;
     weo::Buffer fused_tmp;   // ring of odd-site t-slices
@@ -117,8 +118,10 @@ int launch_hop_f64(int fmt, bool dag, bool axpy, const HopParams &p, const Launc
                    cudaStream_t s);
 int launch_hop_f32(int fmt, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
                    cudaStream_t s);
-int launch_hop_16(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
-                  const LaunchCfg &cfg, cudaStream_t s);
+int launch_hop_h16(int fmt, int io, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
+                   cudaStream_t s);
+int launch_hop_b16(int fmt, int io, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
+                   cudaStream_t s);
 
 // Per-kernel event timing (prof.cu). prof_begin returns a token (-1 when off).
 int prof_begin(wilson_eo_s *h, const char *label, cudaStream_t s);
@@ -150,7 +153,7 @@ int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, 
 int scale_spinor(wilson_eo_s *h, void *v, int nrhs, double c, cudaStream_t s);
 
 // solver.cu
-int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host,
+int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b_host, int nrhs,
                  double tol, int maxiter, int mixed, int *iters_out, double *relres_out,
                  cudaStream_t user);
 int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs);

@@ -11,7 +11,10 @@ int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
     const int threads = cfg.threads;
     dim3 grid((unsigned)((p.vh + threads - 1) / threads), (unsigned)((p.nrhs + R - 1) / R));
-    hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
+    if constexpr (sizeof(typename SOut::real) == 4 && R == 1)
+        hop_kernel_occ<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
+    else
+        hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
