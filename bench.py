@@ -86,7 +86,7 @@ def fields(seed=0):
 
 
 # sources that define the FP32 hopping kernels whose DRAM traffic ncu measured
-HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "dslash_f32.cu")
+HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "weo_launch.cuh", "dslash_f32.cu")
 
 
 def kernel_source_hash(files=HOP_SOURCES):
@@ -271,6 +271,9 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     achieved = algo / (avg_ms * 1e-3) / 1e9
     traffic = stored_traffic(label)
+    # the single hops (D_oe-type, no axpy): 1320 flop per output site, V/2 sites
+    hops = {k: round(1320 * (V // 2) / (ms / cnt * 1e-3) / 1e9, 1)
+            for k, (ms, cnt) in prof.items() if "_axpy" not in k}
     roofline = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -384,7 +387,8 @@ def run_ours(args, rank, world, local):
                        "threads": args.threads, "second_hop_order": "down" if args.order else "up",
                        "l2": "inputs larger than L2 (604 MB of links per hop pass)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roofline, "hop_gflops": hops, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches,
             "clocks": clk.summary(), "check": check, "variants": variants,
             "extras": extra, "solve": solve,
         }

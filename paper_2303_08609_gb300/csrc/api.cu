@@ -364,7 +364,8 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
     if (device_bytes)
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
-                        h->even1.bytes + h->fused_tmp.bytes + h->fused_ctrl.bytes + h->stage_in.bytes +
+                        h->even1.bytes + h->fused_tmp.bytes + h->fused_ctrl.bytes + h->halo.bytes +
+                        h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
 }

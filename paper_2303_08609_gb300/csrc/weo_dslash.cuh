@@ -195,8 +195,9 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
 
 // The same kernel with the register allocation capped at 64 (four CTAs of 256
 // threads per SM, 50 % occupancy): for FP32-arithmetic hops with one
-// right-hand side per thread this measured faster on GB300 than the uncapped
-// 80 registers, despite a few spilled values.
+// right-hand side per thread and 18-real FP32 or 16-bit links this measured
+// faster on GB300 than the uncapped 78-80 registers, despite a few spilled
+// values.
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 __global__ void __launch_bounds__(256, 4) hop_kernel_occ(const HopParams p)
 {

@@ -2,6 +2,8 @@
 // compile-time instance. Included by one translation unit per precision.
 #pragma once
 
+#include <type_traits>
+
 #include "weo_internal.h"
 
 namespace weo {
@@ -11,7 +13,9 @@ int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
     const int threads = cfg.threads;
     dim3 grid((unsigned)((p.vh + threads - 1) / threads), (unsigned)((p.nrhs + R - 1) / R));
-    if constexpr (sizeof(typename SOut::real) == 4 && R == 1)
+    // the 64-register cap pays for 18-real FP32 and 16-bit links; the FP32
+    // 12-real rebuild spills too much under it
+    if constexpr (sizeof(typename SOut::real) == 4 && R == 1 && !std::is_same<Lk, LkF32_12>::value)
         hop_kernel_occ<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
     else
         hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);

@@ -175,3 +175,51 @@ def test_apply_captured_in_cuda_graph(weo):
     torch.cuda.synchronize()
     assert torch.equal(z, ref)
     op.close()
+
+
+def test_batch_launch_captured_in_cuda_graph(weo, oracle_lib):
+    """The cooperative mixed-lattice launch replays from a CUDA graph."""
+    import torch
+
+    specs = [((8, 8, 8, 8), 0.12, 21), ((4, 6, 4, 8), 0.13, 22)]
+    ops, xs, ys, data = [], [], [], []
+    for dims, kappa, seed in specs:
+        U = gen.gauge_field(dims, "haar", seed=seed)
+        psi = gen.gaussian_spinor(dims, seed=seed + 1)[0]
+        ops.append(weo.WilsonEO(dims, kappa, to_device(U), prec="f32"))
+        xs.append(to_device(to_planar(psi), "f32"))
+        ys.append(torch.empty_like(xs[-1]))
+        data.append((U, kappa, psi, dims))
+    hs = [o.handle for o in ops]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        weo.wilson_eo_apply_batch(hs, ys, xs, False, s)  # sizes the buffers
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        weo.wilson_eo_apply_batch(hs, ys, xs, False, s)
+    for y in ys:
+        y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for (U, kappa, psi, dims), y in zip(data, ys):
+        assert rel_l2(from_planar(y.cpu().numpy()), oracle_lib.meo(U, kappa, psi, dims)) <= TOL["f32"]
+    for o in ops:
+        o.close()
+
+
+def test_footprint_16x16x16x16_fp32(weo):
+    """Sec. 4 quotes 18 MiB of FP32 links and 6 MiB per FP32 spinor at 16^4: the
+    handle holds the packed 18-real FP32 links (18 MiB) next to its FP64 copy of
+    the canonical field (2 x 18 MiB), and one apply adds one FP32 odd field
+    (half a 6 MiB full-lattice spinor)."""
+    import torch
+
+    dims = (16, 16, 16, 16)
+    op = weo.WilsonEO(dims, 0.1, to_device(gen.gauge_field(dims, "haar", seed=23)), prec="f32")
+    mib = 2**20
+    assert op.info()["device_bytes"] == 18 * mib + 36 * mib
+    x = torch.zeros((4, 3, op.vh), dtype=torch.complex64, device="cuda")
+    op.apply(x)
+    assert op.info()["device_bytes"] == 18 * mib + 36 * mib + 3 * mib
+    op.close()
