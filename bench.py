@@ -566,10 +566,13 @@ def solve_comparison(dev, dims):
                                     ("mixed_bf16_fused", "bf16", True, 1),
                                     ("mixed_f32_fused", "f32", True, 1),
                                     ("mixed_f16_two_pass", "f16", True, 0),
+                                    ("mixed_f16_two_pass_delta0.03", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0)):
         op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=18)
         if algo:
             weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
+        if "delta" in name:
+            weo.wilson_eo_solver_config(op.handle, delta=float(name.split("delta")[1]))
         try:
             x, info = op.solve(bd, tol=1e-10, maxiter=20000, mixed=mixed)
             res[name] = {k: (round(v, 4) if isinstance(v, float) and k == "seconds" else v)

@@ -127,7 +127,10 @@ __device__ __forceinline__ double re_dot(T2 a, T2 b) { return double(a.x) * b.x 
 #define FOR_ELEMENTS(k) \
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
 
-// mode 0: red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp
+// mode 0: red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp.
+// The solver calls mode 1 with a = b = M p: for A = M^dag M, <p, A p> = |M p|^2,
+// which reads one vector instead of two and cannot come out negative when the
+// low-precision M and M^dag are not exact adjoints of each other.
 template <typename T2>
 __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, long long n,
                                                      SolveScalars *scs, int mode)
@@ -395,13 +398,13 @@ static int cg_iteration(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bo
     SolveScalars *sc = dev_scal(S);
     if (mixed) {
         WEO_TRY(normal_op(h, S, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
-        k_dot<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc, 1);
+        k_dot<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->t32.ptr, (const float2 *)S->t32.ptr, n, sc, 1);
         k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->rs.ptr,
                                                           (const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc);
         k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->p.ptr, (const float2 *)S->rs.ptr, n, sc);
     } else {
         WEO_TRY(normal_op(h, S, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
-        k_dot<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc, 1);
+        k_dot<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->e64.ptr, (const double2 *)S->e64.ptr, n, sc, 1);
         k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->r64.ptr,
                                                            (const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
         k_cg_dir<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->p64.ptr, (const double2 *)S->r64.ptr, n, sc);

@@ -77,3 +77,25 @@ def test_create_rejects_bad_enums_and_nulls(lib):
     assert lib.wilson_eo_apply(None, None, None, 1, None) == -1
     assert lib.wilson_eo_info(None, None, None, None, None, None, None) == -1
     assert weo.STATUS[-1] == "WEO_ERR_ARG"
+
+
+def test_create_rejects_half_volume_beyond_int32(lib):
+    """Site indices are 32-bit inside the kernels: V/2 >= 2^31 is refused up front."""
+    import paper_2303_08609_gb300 as weo
+
+    U = np.zeros((4, 1, 3, 3), dtype=np.complex128)
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_create((2048, 2048, 1024, 2), 0.1, "f32", 18, U)
+    assert e.value.status == -2 and "large" in weo.wilson_eo_last_error()
+
+
+def test_noalloc_rejects_bad_arguments_before_the_device(lib):
+    import paper_2303_08609_gb300 as weo
+
+    z = np.zeros(8, dtype=np.complex64)
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_apply_noalloc((4, 4, 3, 4), 0.1, z, z.copy(), z)
+    assert e.value.status == -2
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_apply_noalloc((64, 64, 64, 64), 0.1, z, z.copy(), z)
+    assert e.value.status == -2 and "349525" in weo.wilson_eo_last_error()
