@@ -216,7 +216,9 @@ def run_ours(args, rank, world, local):
     U, psi = fields()
     V = int(np.prod(DIMS))
     vh = V // 2
-    x_host = np.ascontiguousarray(np.moveaxis(psi, 0, -1)).astype(np.complex64)
+    # the handle's spinor dtype: complex128 for FP64 handles, complex64 otherwise
+    x_host = np.ascontiguousarray(np.moveaxis(psi, 0, -1)).astype(
+        np.complex128 if args.prec == "f64" else np.complex64)
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
     z = torch.empty_like(x)

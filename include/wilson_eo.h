@@ -156,7 +156,9 @@ int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi
  *              with the FP64 operator. Reductions accumulate in FP64.
  * Convergence: |b - A x| / |b| <= tol with the residual recomputed in FP64 from
  * the returned x (true_relres_out). Returns WEO_OK, WEO_ERR_NOT_CONVERGED
- * (maxiter iterations done; x_e holds the last iterate), WEO_ERR_NONFINITE (NaN
+ * (maxiter iterations done, or -- mixed mode -- the true residual grew 10^4-fold
+ * above its best value because the low-precision operator is too far from the
+ * FP64 one; x_e holds the last iterate), WEO_ERR_NONFINITE (NaN
  * or Inf, or a non-positive <p, A p>; x_e is not written) or an argument / CUDA
  * error. tol in (0, 1); maxiter >= 0. Blocks until done; the iterations run on
  * a stream the handle owns after the work already queued on `stream` finished.

@@ -135,6 +135,40 @@ def _ptr(a):
     raise TypeError(f"cannot pass {type(a)} to the C ABI")
 
 
+def _nbytes(a):
+    if isinstance(a, np.ndarray):
+        return a.nbytes
+    if hasattr(a, "element_size"):
+        return a.numel() * a.element_size()
+    return None
+
+
+def _dtype_name(a):
+    return str(getattr(a, "dtype", "")).replace("torch.", "")
+
+
+def _expect(h, arrays, nrhs=1, kind="spinor", where=""):
+    """Refuse arrays whose dtype or size does not match what the library will
+    read or write for handle ``h`` -- the C ABI cannot check sizes itself.
+    kind: "spinor" (handle's spinor dtype), "spinor64" (complex128 spinors),
+    "gauge" (handle's spinor dtype, 4*V*9 complex)."""
+    info = wilson_eo_info(h)
+    vh = info["half_volume"]
+    f64 = info["prec"] == PREC["f64"] or kind == "spinor64"
+    want_dtype = "complex128" if f64 else "complex64"
+    elt = 16 if f64 else 8
+    need = (4 * 2 * vh * 9 * elt) if kind == "gauge" else 12 * vh * nrhs * elt
+    for a in arrays:
+        if a is None or isinstance(a, int):
+            continue
+        dt = _dtype_name(a)
+        if dt and dt != want_dtype:
+            raise TypeError(f"{where}: expected {want_dtype} arrays for this handle, got {dt}")
+        nb = _nbytes(a)
+        if nb is not None and nb < need:
+            raise ValueError(f"{where}: array of {nb} bytes, the call touches {need}")
+
+
 def _stream(stream):
     """cudaStream_t of ``stream``: a torch.cuda.Stream, an int handle, or None
     for torch's current stream (the legacy default stream without torch CUDA)."""
@@ -194,16 +228,19 @@ def wilson_eo_info(h):
 
 
 def wilson_eo_apply(h, out_e, in_e, nrhs=1, stream=None):
+    _expect(h, (out_e, in_e), nrhs, where="wilson_eo_apply")
     _check(_load().wilson_eo_apply(h, _ptr(out_e), _ptr(in_e), int(nrhs), _stream(stream)),
            "wilson_eo_apply")
 
 
 def wilson_eo_apply_dag(h, out_e, in_e, nrhs=1, stream=None):
+    _expect(h, (out_e, in_e), nrhs, where="wilson_eo_apply_dag")
     _check(_load().wilson_eo_apply_dag(h, _ptr(out_e), _ptr(in_e), int(nrhs), _stream(stream)),
            "wilson_eo_apply_dag")
 
 
 def wilson_eo_hop(h, out_parity, dag, out, inp, nrhs=1, stream=None):
+    _expect(h, (out, inp), nrhs, where="wilson_eo_hop")
     _check(_load().wilson_eo_hop(h, int(out_parity), int(bool(dag)), _ptr(out), _ptr(inp),
                                  int(nrhs), _stream(stream)), "wilson_eo_hop")
 
@@ -235,11 +272,15 @@ def wilson_eo_profile_read(h, reset=True, max_kernels=64):
 
 
 def wilson_eo_link_grad(h, grad, g_e, phi_e, stream=None):
+    _expect(h, (g_e, phi_e), 1, where="wilson_eo_link_grad")
+    _expect(h, (grad,), kind="gauge", where="wilson_eo_link_grad")
     _check(_load().wilson_eo_link_grad(h, _ptr(grad), _ptr(g_e), _ptr(phi_e), _stream(stream)),
            "wilson_eo_link_grad")
 
 
 def wilson_eo_force(h, force, dS_dphi_e, phi_e, stream=None):
+    _expect(h, (dS_dphi_e, phi_e), 1, where="wilson_eo_force")
+    _expect(h, (force,), kind="gauge", where="wilson_eo_force")
     _check(_load().wilson_eo_force(h, _ptr(force), _ptr(dS_dphi_e), _ptr(phi_e), _stream(stream)),
            "wilson_eo_force")
 
@@ -247,6 +288,16 @@ def wilson_eo_force(h, force, dS_dphi_e, phi_e, stream=None):
 def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=None):
     """FP32 M_eo (or M_eo^dag) on caller-owned device arrays; the library
     allocates nothing for it (see the header for the scratch-array rules)."""
+    V = int(np.prod([int(x) for x in dims]))
+    for a, need, what in ((gauge, 4 * V * 9 * 8, "gauge"), (out_e, 6 * V * 8, "out_e"),
+                          (in_e, 6 * V * 8, "in_e")):
+        dt = _dtype_name(a)
+        if dt and dt != "complex64":
+            raise TypeError(f"wilson_eo_apply_noalloc: {what} must be complex64, got {dt}")
+        nb = _nbytes(a)
+        valid_dims = all(int(x) >= 2 and int(x) % 2 == 0 for x in dims)
+        if nb is not None and nb < need and valid_dims and V // 2 <= 349525:
+            raise ValueError(f"wilson_eo_apply_noalloc: {what} has {nb} bytes, needs {need}")
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     _check(_load().wilson_eo_apply_noalloc(d, float(kappa), _ptr(gauge), _ptr(out_e), _ptr(in_e),
                                            int(bool(dag)), _stream(stream)),
@@ -257,6 +308,7 @@ def wilson_eo_solve(h, x_e, b_e, tol=1e-10, maxiter=10000, mixed=True, stream=No
                     raise_on_error=True):
     """Solve M^dag M x = b in place on ``x_e`` (complex128). Returns
     ``(status, iterations, true_relres)``."""
+    _expect(h, (x_e, b_e), 1, kind="spinor64", where="wilson_eo_solve")
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     st = _load().wilson_eo_solve(h, _ptr(x_e), _ptr(b_e), float(tol), int(maxiter),
@@ -268,11 +320,13 @@ def wilson_eo_solve(h, x_e, b_e, tol=1e-10, maxiter=10000, mixed=True, stream=No
 
 
 def wilson_eo_prepare_source(h, rhs_e, eta_e, eta_o, stream=None):
+    _expect(h, (rhs_e, eta_e, eta_o), 1, where="wilson_eo_prepare_source")
     _check(_load().wilson_eo_prepare_source(h, _ptr(rhs_e), _ptr(eta_e), _ptr(eta_o),
                                             _stream(stream)), "wilson_eo_prepare_source")
 
 
 def wilson_eo_reconstruct(h, xi_o, eta_o, xi_e, stream=None):
+    _expect(h, (xi_o, eta_o, xi_e), 1, where="wilson_eo_reconstruct")
     _check(_load().wilson_eo_reconstruct(h, _ptr(xi_o), _ptr(eta_o), _ptr(xi_e), _stream(stream)),
            "wilson_eo_reconstruct")
 
@@ -281,6 +335,7 @@ def wilson_eo_solve_full(h, xi_e, xi_o, eta_e, eta_o, tol=1e-10, maxiter=10000, 
                          stream=None, raise_on_error=True):
     """D_W xi = eta (complex128 planar even/odd parts); xi_e holds the guess.
     Returns (status, iterations, even-system relres)."""
+    _expect(h, (xi_e, xi_o, eta_e, eta_o), 1, kind="spinor64", where="wilson_eo_solve_full")
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     st = _load().wilson_eo_solve_full(h, _ptr(xi_e), _ptr(xi_o), _ptr(eta_e), _ptr(eta_o),
@@ -295,6 +350,7 @@ def wilson_eo_solve_multi(h, x_e, b_e, nrhs, tol=1e-10, maxiter=10000, mixed=Tru
                           raise_on_error=True):
     """Solve nrhs systems M^dag M x_r = b_r in lockstep (complex128 planar, in place
     on ``x_e``). Returns ``(status, iterations[nrhs], true_relres[nrhs])``."""
+    _expect(h, (x_e, b_e), nrhs, kind="spinor64", where="wilson_eo_solve_multi")
     it = (ctypes.c_int * nrhs)()
     rr = (ctypes.c_double * nrhs)()
     st = _load().wilson_eo_solve_multi(h, _ptr(x_e), _ptr(b_e), int(nrhs), float(tol), int(maxiter),
@@ -323,6 +379,8 @@ def wilson_eo_apply_batch(handles, outs, ins, dag=False, stream=None):
     n = len(handles)
     if not (len(outs) == len(ins) == n):
         raise ValueError("handles, outs and ins must have the same length")
+    for h, o, i in zip(handles, outs, ins):
+        _expect(h, (o, i), 1, where="wilson_eo_apply_batch")
     P = ctypes.c_void_p
     hs = (P * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     os_ = (P * n)(*[_ptr(o).value for o in outs])
@@ -357,11 +415,13 @@ def wilson_eo_get_algorithm(h):
 def wilson_eo_hop_split(h, ranks, out_parity, dag, out, inp, stream=None):
     """Hopping term with the lattice split along t into `ranks` sub-domains and
     every crossing hop exchanged through face buffers (forced self-exchange)."""
+    _expect(h, (out, inp), 1, where="wilson_eo_hop_split")
     _check(_load().wilson_eo_hop_split(h, int(ranks), int(out_parity), int(bool(dag)), _ptr(out),
                                        _ptr(inp), _stream(stream)), "wilson_eo_hop_split")
 
 
 def wilson_eo_inject_fused_timeout(h, out_e, in_e, stream=None):
+    _expect(h, (out_e, in_e), 1, where="wilson_eo_inject_fused_timeout")
     _check(_load().wilson_eo_inject_fused_timeout(h, _ptr(out_e), _ptr(in_e), _stream(stream)),
            "wilson_eo_inject_fused_timeout")
 

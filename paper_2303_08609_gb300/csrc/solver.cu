@@ -40,6 +40,9 @@ constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
 constexpr int kMaxBreakdowns = 64;  // direction restarts before a solve gives up
 constexpr int kMaxRhs = 64;
+// a true residual this many times above the smallest one seen means the
+// low-precision iteration is diverging from the FP64 system: give up
+constexpr double kDivergence = 1e4;
 
 struct SolveScalars {
     double rr;       // |r|^2 of the iterated residual
@@ -492,7 +495,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
     for (int r = 0; r < R; ++r) WEO_TRY(set_flag(S, r, offsetof(SolveScalars, active), 1));
     S->iterations = S->reliable_updates = S->hi_applies = 0;
     std::vector<int> active(R, 1), iters(R, 0);
-    std::vector<double> target(R), rr_true(R), r_max(R);
+    std::vector<double> target(R), rr_true(R), r_max(R), rr_min(R);
 
     // |b|^2 of every right-hand side
     k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->b64.ptr, n, sc, 0);
@@ -521,6 +524,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         rr_true[r] = S->host[r].red;
         if (!isfinite(rr_true[r])) return set_error(WEO_ERR_NONFINITE, "non-finite initial residual");
         r_max[r] = sqrt(rr_true[r]);
+        rr_min[r] = rr_true[r];
         if (bb[r] == 0.0 || rr_true[r] <= target[r]) WEO_TRY(retire(r));
     }
     int breakdowns = 0;
@@ -612,12 +616,26 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
             WEO_CUDA(cudaGetLastError());
             WEO_TRY(true_residual(h, S, *ghi));
             S->reliable_updates += 1;
+            bool diverging = false;
             for (int r = 0; r < R; ++r) {
                 if (!active[r]) continue;
                 rr_true[r] = S->host[r].red;
                 if (!isfinite(rr_true[r])) return set_error(WEO_ERR_NONFINITE, "non-finite true residual");
                 if (rr_true[r] <= target[r]) WEO_TRY(retire(r));
                 else r_max[r] = sqrt(rr_true[r]);
+                rr_min[r] = std::min(rr_min[r], rr_true[r]);
+                if (rr_true[r] > kDivergence * kDivergence * rr_min[r]) diverging = true;
+            }
+            if (diverging) {
+                for (int r = 0; r < R; ++r)
+                    if (active[r]) iters[r] = S->iterations;
+                if (iters_out)
+                    for (int r = 0; r < R; ++r) iters_out[r] = active[r] ? S->iterations : iters[r];
+                if (relres_out)
+                    for (int r = 0; r < R; ++r) relres_out[r] = bb[r] > 0.0 ? sqrt(rr_true[r] / bb[r]) : 0.0;
+                return set_error(WEO_ERR_NOT_CONVERGED,
+                                 "the low-precision iteration diverges from the FP64 system (true residual "
+                                 "grew 1e4-fold); its operator is too far from the FP64 one");
             }
             if (n_active == 0) break;
             k_convert<float2, double2><<<flat_grid(nt), 256, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, nt);
