@@ -33,10 +33,12 @@
  *   force   F[mu][lex][a][b]         like the gauge field, in the spinor dtype
  *
  * Pointers: every array argument may be device memory (cudaMalloc / torch) or
- * host memory (pageable or pinned). Host arrays are staged through buffers the
- * handle owns; a call with any host array blocks until its results are in host
- * memory. Calls on device arrays are asynchronous on `stream` (a cudaStream_t,
- * NULL = the legacy default stream) unless stated otherwise.
+ * host memory. Host arrays are copied through buffers the handle owns, on
+ * `stream`. Calls are asynchronous on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream) unless stated otherwise: with device or page-locked
+ * (pinned) host arrays the caller synchronises the stream before reading an
+ * output; a pageable host output is complete when the call returns, and a
+ * pageable host input may be reused as soon as the call returns.
  *
  * Ownership: the caller owns every array it passes. The handle owns its packed
  * gauge copies, its intermediate odd-site fields, solver workspaces, staging

@@ -52,7 +52,22 @@ static bool is_device_pointer(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Input array: device pointers pass through, host arrays are copied into `buf`.
+// page-locked host memory (cudaHostAlloc / cudaHostRegister / torch pin_memory)
+static bool is_pinned_host_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Input array: device pointers pass through, host arrays are copied into `buf`
+// on the stream. No host synchronisation is needed: the next call on the
+// handle's stream runs after the kernels that read `buf`, and a pageable
+// source may be reused as soon as cudaMemcpyAsync returns.
 static int stage_in(Buffer &buf, const void *p, size_t bytes, cudaStream_t s, const void **dev)
 {
     if (is_device_pointer(p)) {
@@ -66,7 +81,7 @@ static int stage_in(Buffer &buf, const void *p, size_t bytes, cudaStream_t s, co
 }
 
 // Output array: device pointers pass through, host arrays get a device buffer
-// whose contents finish_out copies back (blocking).
+// whose contents finish_out copies back on the stream.
 static int stage_out(Buffer &buf, void *p, size_t bytes, void **dev, bool *host)
 {
     *host = !is_device_pointer(p);
@@ -79,11 +94,14 @@ static int stage_out(Buffer &buf, void *p, size_t bytes, void **dev, bool *host)
     return WEO_OK;
 }
 
+// Copy a staged output back. Pinned host memory: asynchronous like device
+// memory (the caller synchronises the stream before reading). Pageable host
+// memory: the call returns once the result is there.
 static int finish_out(void *host_ptr, const void *dev, size_t bytes, bool host, cudaStream_t s)
 {
     if (!host) return WEO_OK;
     WEO_CUDA(cudaMemcpyAsync(host_ptr, dev, bytes, cudaMemcpyDeviceToHost, s));
-    WEO_CUDA(cudaStreamSynchronize(s));
+    if (!is_pinned_host_pointer(host_ptr)) WEO_CUDA(cudaStreamSynchronize(s));
     return WEO_OK;
 }
 
@@ -212,7 +230,6 @@ static int apply_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, 
     WEO_TRY(stage_in(h->stage_in, in_e, bytes, s, &in));
     WEO_TRY(stage_out(h->stage_out, out_e, bytes, &out, &out_host));
     WEO_TRY(meo_device(h, out, in, nrhs, dag, s));
-    if (!out_host && in != in_e) WEO_CUDA(cudaStreamSynchronize(s));
     return finish_out(out_e, out, bytes, out_host, s);
 }
 
@@ -417,7 +434,6 @@ int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void 
         p.out = dout;
         p.out_stride = (long long)ext;
         WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, dag != 0, false, p, s));
-        if (!out_host && din != in) WEO_CUDA(cudaStreamSynchronize(s));
         return finish_out(out, dout, bytes, out_host, s);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_hop");
@@ -442,7 +458,6 @@ int wilson_eo_link_grad(wilson_eo_t h, void *grad, const void *g_e, const void *
         WEO_TRY(stage_in(h->even1, phi_e, sb, s, &phi));
         WEO_TRY(stage_out(h->stage_aux, grad, gb, &out, &out_host));
         WEO_TRY(link_grad_device(h, out, g, phi, 0, s));
-        if (!out_host && (g != g_e || phi != phi_e)) WEO_CUDA(cudaStreamSynchronize(s));
         return finish_out(grad, out, gb, out_host, s);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_link_grad");
@@ -471,7 +486,6 @@ int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi
         WEO_TRY(scale_spinor(h, h->even1.ptr, 1, 2.0, s));
         WEO_TRY(link_grad_device(h, out, h->even1.ptr, phi, 1, s));
         if (dphi) WEO_TRY(meo_device(h, dphi, h->even1.ptr, 1, true, s));  // 2 M^dag M phi
-        if (!out_host && !dphi_host && phi != phi_e) WEO_CUDA(cudaStreamSynchronize(s));
         if (dphi) WEO_TRY(finish_out(dS_dphi_e, dphi, sb, dphi_host, s));
         return finish_out(force, out, gb, out_host, s);
     } catch (...) {
@@ -539,7 +553,6 @@ static int source_op(wilson_eo_t h, void *out, const void *in_a, const void *in_
     WEO_TRY(stage_in(h->even1, in_b, b, s, &c));
     WEO_TRY(stage_out(h->stage_out, out, b, &o, &oh));
     WEO_TRY(prepare ? prepare_source_device(h, o, a, c, s) : reconstruct_device(h, o, a, c, s));
-    if (!oh && (a != in_a || c != in_b)) WEO_CUDA(cudaStreamSynchronize(s));
     return finish_out(out, o, b, oh, s);
 }
 

@@ -73,6 +73,9 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(weo):
         weo.wilson_eo_apply_noalloc(dims, 0.1, U, y, x)
     assert e.value.status == -2
     assert "349525" in weo.wilson_eo_last_error()
+    # host arrays are refused by the library itself (staging them would allocate)
+    Uh = torch.zeros((4, 8**4, 3, 3), dtype=torch.complex64)
+    xd = torch.zeros((4, 3, 8**4 // 2), dtype=torch.complex64, device="cuda")
     with pytest.raises(weo.WilsonEOError) as e:
-        weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, U.cpu(), y, x)
+        weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, Uh, torch.empty_like(xd), xd)
     assert e.value.status == -1
