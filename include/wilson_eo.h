@@ -227,6 +227,12 @@ int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
 int wilson_eo_apply_batch(int n, const wilson_eo_t *hs, void *const *outs,
                           const void *const *ins, int dag, void *stream);
 
+/* wilson_eo_apply_batch with nrhs[k] (1..1024) right-hand sides for lattice k
+ * (outs[k], ins[k] hold nrhs[k] canonical even spinors), still one cooperative
+ * launch; for FP32 handles two right-hand sides share each link load. */
+int wilson_eo_apply_batch_rhs(int n, const wilson_eo_t *hs, void *const *outs,
+                              const void *const *ins, const int *nrhs, int dag, void *stream);
+
 /* Autotune M_eo on this handle with nrhs right-hand sides: every candidate is
  * timed with CUDA events on `stream` and the fastest is kept -- the two-launch
  * algorithm with threads 64/128/192/256 per CTA and 1, 2 or 4 right-hand sides

@@ -86,6 +86,8 @@ def _load():
         "wilson_eo_solve_stats": (I, [P, IP, IP, IP, ctypes.POINTER(D)]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(P), I, P]),
+        "wilson_eo_apply_batch_rhs": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                          ctypes.POINTER(P), IP, I, P]),
         "wilson_eo_tune": (I, [P, I, IP, IP, ctypes.POINTER(D), P]),
         "wilson_eo_get_launch": (I, [P, IP, IP]),
         "wilson_eo_set_algorithm": (I, [P, I, I, I]),
@@ -387,6 +389,22 @@ def wilson_eo_apply_batch(handles, outs, ins, dag=False, stream=None):
     is_ = (P * n)(*[_ptr(i).value for i in ins])
     _check(_load().wilson_eo_apply_batch(n, hs, os_, is_, int(bool(dag)), _stream(stream)),
            "wilson_eo_apply_batch")
+
+
+def wilson_eo_apply_batch_rhs(handles, outs, ins, nrhs, dag=False, stream=None):
+    """Several lattices with nrhs[k] right-hand sides each, in one persistent launch."""
+    n = len(handles)
+    if not (len(outs) == len(ins) == len(nrhs) == n):
+        raise ValueError("handles, outs, ins and nrhs must have the same length")
+    for h, o, i, r in zip(handles, outs, ins, nrhs):
+        _expect(h, (o, i), int(r), where="wilson_eo_apply_batch_rhs")
+    P = ctypes.c_void_p
+    hs = (P * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    os_ = (P * n)(*[_ptr(o).value for o in outs])
+    is_ = (P * n)(*[_ptr(i).value for i in ins])
+    rs = (ctypes.c_int * n)(*[int(r) for r in nrhs])
+    _check(_load().wilson_eo_apply_batch_rhs(n, hs, os_, is_, rs, int(bool(dag)), _stream(stream)),
+           "wilson_eo_apply_batch_rhs")
 
 
 def wilson_eo_tune(h, nrhs=1, stream=None):

@@ -1,9 +1,11 @@
 // Mixed-lattice batch: M_eo (or M_eo^dag) on several lattices -- each with its
-// own extents, kappa and links -- in ONE persistent cooperative launch. The grid
-// (a whole number of CTAs per SM, all resident) walks the CTA-sized tiles of
-// every lattice's first hop, synchronises once across the grid, then walks the
-// tiles of every second hop (with the axpy of Eq. 4). Lattices need not have a
-// size that fills the GPU on its own: small and large lattices share one launch.
+// own extents, kappa, links and number of right-hand sides -- in ONE persistent
+// cooperative launch. The grid (a whole number of CTAs per SM, all resident)
+// walks the tiles of every lattice's first hop, synchronises once across the
+// grid, then walks the tiles of every second hop (with the axpy of Eq. 4). A
+// tile is CTA-sized in sites and covers R right-hand sides, which share each
+// link load. Lattices need not fill the GPU on their own: small and large
+// lattices share one launch.
 #include <cooperative_groups.h>
 
 #include <vector>
@@ -19,7 +21,8 @@ constexpr int kBatchThreads = 128;
 
 struct BatchArgs {
     int n;
-    long long tile_begin[kMaxBatch + 1];  // prefix sums of CTA tiles per lattice
+    long long tile_begin[kMaxBatch + 1];  // prefix sums of tiles per lattice
+    int site_tiles[kMaxBatch];            // CTA-sized site blocks per right-hand-side block
     HopParams first[kMaxBatch];           // H_oe onto odd sites
     HopParams second[kMaxBatch];          // in - kappa^2 H_eo tmp onto even sites
 };
@@ -31,27 +34,31 @@ __device__ __forceinline__ int find_lattice(const BatchArgs &a, long long tile)
     return k;
 }
 
-template <class Sp, class Lk, bool Dag>
+template <class Sp, class Lk, bool Dag, int R>
 __global__ void __launch_bounds__(kBatchThreads) batch_meo_kernel(const __grid_constant__ BatchArgs a)
 {
     const long long total = a.tile_begin[a.n];
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int k = find_lattice(a, tile);
-        const long long site = (tile - a.tile_begin[k]) * kBatchThreads + threadIdx.x;
-        if (site < a.first[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, false, 1>(a.first[k], (int)site, 0);
+        const long long local = tile - a.tile_begin[k];
+        const int rb = (int)(local / a.site_tiles[k]);
+        const long long site = (local - (long long)rb * a.site_tiles[k]) * kBatchThreads + threadIdx.x;
+        if (site < a.first[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, false, R>(a.first[k], (int)site, rb * R);
     }
     cg::this_grid().sync();
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int k = find_lattice(a, tile);
-        const long long site = (tile - a.tile_begin[k]) * kBatchThreads + threadIdx.x;
-        if (site < a.second[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, true, 1>(a.second[k], (int)site, 0);
+        const long long local = tile - a.tile_begin[k];
+        const int rb = (int)(local / a.site_tiles[k]);
+        const long long site = (local - (long long)rb * a.site_tiles[k]) * kBatchThreads + threadIdx.x;
+        if (site < a.second[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, true, R>(a.second[k], (int)site, rb * R);
     }
 }
 
-template <class Sp, class Lk, bool Dag>
+template <class Sp, class Lk, bool Dag, int R>
 static int launch_batch(const BatchArgs &a, cudaStream_t s)
 {
-    auto kern = batch_meo_kernel<Sp, Lk, Dag>;
+    auto kern = batch_meo_kernel<Sp, Lk, Dag, R>;
     int dev = 0, sms = 0, per_sm = 0;
     WEO_CUDA(cudaGetDevice(&dev));
     WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -73,9 +80,73 @@ static int launch_batch(const BatchArgs &a, cudaStream_t s)
 }
 
 template <class Sp, class Lk>
-static int launch_batch_dag(const BatchArgs &a, bool dag, cudaStream_t s)
+static int launch_batch_dag(const BatchArgs &a, bool dag, int R, cudaStream_t s)
 {
-    return dag ? launch_batch<Sp, Lk, true>(a, s) : launch_batch<Sp, Lk, false>(a, s);
+    if (R == 2) return dag ? launch_batch<Sp, Lk, true, 2>(a, s) : launch_batch<Sp, Lk, false, 2>(a, s);
+    return dag ? launch_batch<Sp, Lk, true, 1>(a, s) : launch_batch<Sp, Lk, false, 1>(a, s);
+}
+
+static int apply_batch_impl(int n, const wilson_eo_t *hs, void *const *outs, const void *const *ins,
+                            const int *nrhs, int dag, void *stream)
+{
+    if (n < 1 || n > kMaxBatch) return set_error(WEO_ERR_ARG, "batch size must be in 1..24");
+    if (!hs || !outs || !ins) return set_error(WEO_ERR_ARG, "NULL array of handles or fields");
+    const int prec = hs[0] ? hs[0]->prec : -1, fmt = hs[0] ? hs[0]->fmt : -1;
+    int dev = 0;
+    WEO_CUDA(cudaGetDevice(&dev));
+    int max_rhs = 1;
+    for (int k = 0; k < n; ++k) {
+        if (!hs[k] || !outs[k] || !ins[k]) return set_error(WEO_ERR_ARG, "NULL handle or field in batch");
+        if (nrhs && (nrhs[k] < 1 || nrhs[k] > 1024)) return set_error(WEO_ERR_ARG, "nrhs per lattice must be in 1..1024");
+        if (hs[k]->prec != prec || hs[k]->fmt != fmt)
+            return set_error(WEO_ERR_UNSUPPORTED, "a batch needs one precision and link format");
+        if (hs[k]->device != dev) return set_error(WEO_ERR_ARG, "batch handles must live on the current device");
+        if (outs[k] == ins[k]) return set_error(WEO_ERR_ARG, "out must not alias in");
+        for (int j = 0; j < k; ++j)
+            if (hs[j] == hs[k]) return set_error(WEO_ERR_ARG, "a handle appears twice in the batch");
+        if (nrhs && nrhs[k] > max_rhs) max_rhs = nrhs[k];
+    }
+    if (prec != WEO_F32 && prec != WEO_F64)
+        return set_error(WEO_ERR_UNSUPPORTED, "batches are provided for FP64 and FP32 handles");
+    // FP32 lattices with several right-hand sides share each link load over two
+    const int R = (prec == WEO_F32 && max_rhs >= 2) ? 2 : 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.tile_begin[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        wilson_eo_s *h = hs[k];
+        const int nr = nrhs ? nrhs[k] : 1;
+        const long long ext = h->vh * (prec == WEO_F64 ? 192 : 96);
+        WEO_TRY(h->tmp.ensure((size_t)ext * nr));
+        HopParams p = geom_params(h);
+        p.nrhs = nr;
+        p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
+        p.gauge_pb = h->gauge.pb;
+        p.in_stride = p.out_stride = p.x_stride = ext;
+        p.out_parity = 1;
+        p.in = ins[k];
+        p.out = h->tmp.ptr;
+        a.first[k] = p;
+        p.out_parity = 0;
+        p.in = h->tmp.ptr;
+        p.out = outs[k];
+        p.x = ins[k];
+        p.a = -h->kappa * h->kappa;
+        a.second[k] = p;
+        a.site_tiles[k] = (int)((h->vh + kBatchThreads - 1) / kBatchThreads);
+        a.tile_begin[k + 1] = a.tile_begin[k] + (long long)a.site_tiles[k] * ((nr + R - 1) / R);
+    }
+    const bool c = fmt == WEO_LINK12;
+    int tok = prof_begin(hs[0], "batch_meo", s);
+    int st;
+    if (prec == WEO_F64)
+        st = c ? launch_batch_dag<SpF64, LkF64_12>(a, dag != 0, 1, s) : launch_batch_dag<SpF64, LkF64_18>(a, dag != 0, 1, s);
+    else
+        st = c ? launch_batch_dag<SpF32, LkF32_12>(a, dag != 0, R, s) : launch_batch_dag<SpF32, LkF32_18>(a, dag != 0, R, s);
+    prof_end(hs[0], tok, s);
+    return st;
 }
 
 }  // namespace weo
@@ -86,58 +157,20 @@ extern "C" int wilson_eo_apply_batch(int n, const wilson_eo_t *hs, void *const *
                                      const void *const *ins, int dag, void *stream)
 {
     try {
-        if (n < 1 || n > kMaxBatch) return set_error(WEO_ERR_ARG, "batch size must be in 1..24");
-        if (!hs || !outs || !ins) return set_error(WEO_ERR_ARG, "NULL array of handles or fields");
-        const int prec = hs[0] ? hs[0]->prec : -1, fmt = hs[0] ? hs[0]->fmt : -1;
-        int dev = 0;
-        WEO_CUDA(cudaGetDevice(&dev));
-        for (int k = 0; k < n; ++k) {
-            if (!hs[k] || !outs[k] || !ins[k]) return set_error(WEO_ERR_ARG, "NULL handle or field in batch");
-            if (hs[k]->prec != prec || hs[k]->fmt != fmt)
-                return set_error(WEO_ERR_UNSUPPORTED, "a batch needs one precision and link format");
-            if (hs[k]->device != dev) return set_error(WEO_ERR_ARG, "batch handles must live on the current device");
-            if (outs[k] == ins[k]) return set_error(WEO_ERR_ARG, "out must not alias in");
-            for (int j = 0; j < k; ++j)
-                if (hs[j] == hs[k]) return set_error(WEO_ERR_ARG, "a handle appears twice in the batch");
-        }
-        if (prec != WEO_F32 && prec != WEO_F64)
-            return set_error(WEO_ERR_UNSUPPORTED, "batches are provided for FP64 and FP32 handles");
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        BatchArgs a;
-        memset(&a, 0, sizeof(a));
-        a.n = n;
-        a.tile_begin[0] = 0;
-        for (int k = 0; k < n; ++k) {
-            wilson_eo_s *h = hs[k];
-            const long long ext = h->vh * (prec == WEO_F64 ? 192 : 96);
-            WEO_TRY(h->tmp.ensure((size_t)ext));
-            HopParams p = geom_params(h);
-            p.nrhs = 1;
-            p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
-            p.gauge_pb = h->gauge.pb;
-            p.in_stride = p.out_stride = p.x_stride = ext;
-            p.out_parity = 1;
-            p.in = ins[k];
-            p.out = h->tmp.ptr;
-            a.first[k] = p;
-            p.out_parity = 0;
-            p.in = h->tmp.ptr;
-            p.out = outs[k];
-            p.x = ins[k];
-            p.a = -h->kappa * h->kappa;
-            a.second[k] = p;
-            a.tile_begin[k + 1] = a.tile_begin[k] + (h->vh + kBatchThreads - 1) / kBatchThreads;
-        }
-        const bool c = fmt == WEO_LINK12;
-        int tok = prof_begin(hs[0], "batch_meo", s);
-        int st;
-        if (prec == WEO_F64)
-            st = c ? launch_batch_dag<SpF64, LkF64_12>(a, dag != 0, s) : launch_batch_dag<SpF64, LkF64_18>(a, dag != 0, s);
-        else
-            st = c ? launch_batch_dag<SpF32, LkF32_12>(a, dag != 0, s) : launch_batch_dag<SpF32, LkF32_18>(a, dag != 0, s);
-        prof_end(hs[0], tok, s);
-        return st;
+        return apply_batch_impl(n, hs, outs, ins, nullptr, dag, stream);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply_batch");
+    }
+}
+
+extern "C" int wilson_eo_apply_batch_rhs(int n, const wilson_eo_t *hs, void *const *outs,
+                                         const void *const *ins, const int *nrhs, int dag,
+                                         void *stream)
+{
+    try {
+        if (!nrhs) return set_error(WEO_ERR_ARG, "nrhs is NULL");
+        return apply_batch_impl(n, hs, outs, ins, nrhs, dag, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply_batch_rhs");
     }
 }
