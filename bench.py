@@ -204,6 +204,19 @@ def algo_bytes_per_site(label):
     return n_sp * sp / 2 + 4 * lk
 
 
+# minimal traffic of one M_eo per lattice site V: the even input once, every
+# link once and the even output once (the odd intermediate never leaves the
+# chip). Against it, the "useful-work" fraction credits fusion and compression.
+def useful_bytes_per_site(prec, fmt):
+    sp = {"f64": 192, "f32": 96, "f16": 52, "bf16": 52}[prec]
+    lk = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[prec]
+    if fmt == 12:
+        lk = lk * 2 // 3
+    if prec in ("f16", "bf16"):
+        sp = 96  # the API's spinors are FP32 for 16-bit handles
+    return sp / 2 + 4 * lk + sp / 2
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -275,15 +288,21 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = measured_peaks()
     achieved = algo / (avg_ms * 1e-3) / 1e9
     traffic = stored_traffic(label)
-    # the single hops (D_oe-type, no axpy): 1320 flop per output site, V/2 sites
-    hops = {k: round(1320 * (V // 2) / (ms / cnt * 1e-3) / 1e9, 1)
-            for k, (ms, cnt) in prof.items() if "_axpy" not in k}
+    # the single hops (D_oe-type, no axpy): 1320 flop per output site, V/2 sites;
+    # the second hops add kappa^2 scale and the subtraction: 1368 per output site
+    hops = {k: round((1368 if "_axpy" in k else 1320) * (V // 2) / (ms / cnt * 1e-3) / 1e9, 1)
+            for k, (ms, cnt) in prof.items()}
+    useful = useful_bytes_per_site(args.prec, args.linkfmt)
     roofline = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": int(algo), "avg_launch_ms": round(avg_ms, 5),
                 "kernel_share": {k: round(v[0] / sum(w[0] for w in prof.values()), 4)
-                                 for k, v in sorted(prof.items())}}
+                                 for k, v in sorted(prof.items())},
+                "useful_work": {"model": f"minimal traffic of M_eo (input, links, output once): "
+                                         f"{useful:g} B per site",
+                                "bytes_per_step": int(2 * useful * V),
+                                "frac": round(2 * useful * V / (ms_step * 1e-3) / 1e9 / peak, 4)}}
 
     # ---- sampled parity of this run's output (M_eo^dag M_eo at 64 sites)
     check = None
@@ -349,6 +368,14 @@ def run_ours(args, rank, world, local):
     op3.close()
     del op2, op3
 
+    # ---- measured FMA peaks (the FP64 kernels are bound by the FP64 pipe)
+    alu_peaks = {}
+    try:
+        alu_peaks = {"f64_tflops": round(weo.wilson_eo_alu_peak("f64") / 1e12, 3),
+                     "f32_tflops": round(weo.wilson_eo_alu_peak("f32") / 1e12, 2)}
+    except Exception as exc:  # pragma: no cover
+        alu_peaks = {"error": repr(exc)}
+
     # ---- other storage formats (same workload, M_eo^dag M_eo per step)
     variants = {}
     if not args.no_variants:
@@ -385,7 +412,11 @@ def run_ours(args, rank, world, local):
             ab = algo_bytes_per_site(lab)
             ent = {"gflops": round(flops_step / (vms * 1e-3) / 1e9, 1),
                    "ms_per_step": round(vms, 4), "dominant_kernel": lab,
-                   "kernel_gbs": round(ab * V / (km / kc * 1e-3) / 1e9, 1) if ab else None}
+                   "kernel_gbs": round(ab * V / (km / kc * 1e-3) / 1e9, 1) if ab else None,
+                   "useful_work_frac": round(2 * useful_bytes_per_site(prec, fmt) * V
+                                             / (vms * 1e-3) / 1e9 / peak, 4)}
+            if prec == "f64" and alu_peaks.get("f64_tflops"):
+                ent["fp64_alu_frac"] = round(ent["gflops"] / (alu_peaks["f64_tflops"] * 1e3), 4)
             yo = np.moveaxis(yv[:, :, torch.from_numpy(sites).to(dev)].cpu().numpy(), -1, 0) \
                 if rank == 0 and check and "error" not in check else None
             if yo is not None:
@@ -423,9 +454,10 @@ def run_ours(args, rank, world, local):
                        "threads": args.threads, "second_hop_order": "down" if args.order else "up",
                        "l2": "inputs larger than L2 (604 MB of links per hop pass)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gflops_1368_per_site": round(value * 1368 / FLOP_PER_SITE, 1),
             "roofline": roofline, "hop_gflops": hops, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches,
-            "clocks": clk.summary(), "check": check, "variants": variants,
+            "clocks": clk.summary(), "check": check, "alu_peaks": alu_peaks, "variants": variants,
             "extras": extra, "solve": solve,
         }
         print(json.dumps(out), flush=True)
@@ -629,51 +661,102 @@ def solve_comparison(dev, dims, only=None):
     return res
 
 
-def cpu_baseline(U, psi, reps=1):
-    """The FP64 oracle (OpenMP over all host cores) on the full workload step."""
+def cpu_model():
+    """Host CPU model as lscpu reports it (Grace reports its Neoverse core)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def slab(U, psi, T):
+    """The workload's first T time slices as a periodic Lx x Ly x Lz x T lattice:
+    every site does the same work as in the full lattice (only the wrap in t
+    differs), so its throughput samples the full workload's."""
+    lx, ly, lz, lt = DIMS
+    V3 = lx * ly * lz
+    Us = np.ascontiguousarray(U.reshape(4, lt, V3, 3, 3)[:, :T].reshape(4, T * V3, 3, 3))
+    return Us, np.ascontiguousarray(psi[: T * V3 // 2]), (lx, ly, lz, T)
+
+
+def oracle_step_seconds(U, psi, dims, reps):
+    import oracle
+
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        yv = oracle.meo(U, KAPPA, psi, dims)
+        oracle.meo_dag(U, KAPPA, yv, dims)
+    return (time.perf_counter() - t0) / reps
+
+
+def cpu_baseline(U, psi, reps=3):
+    """The FP64 oracle on the workload step: OpenMP over all host cores on the full
+    32^3 x 64 lattice, and one thread on an 8-slice sample of it."""
     import oracle
 
     threads = os.cpu_count() or 1
-    oracle.set_threads(threads)
     V = int(np.prod(DIMS))
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        yv = oracle.meo(U, KAPPA, psi, DIMS)
-        oracle.meo_dag(U, KAPPA, yv, DIMS)
-    dt = (time.perf_counter() - t0) / reps
+    oracle.set_threads(threads)
+    dt = oracle_step_seconds(U, psi, DIMS, reps)
+    used = oracle.get_threads()
+    oracle.set_threads(1)
+    Us, ps, sd = slab(U, psi, min(8, DIMS[3]))
+    dt1 = oracle_step_seconds(Us, ps, sd, 1)
+    oracle.set_threads(threads)
     return {"value": round(2 * FLOP_PER_SITE * V / dt / 1e9, 3), "unit": "GFlop/s",
-            "cores": oracle.get_threads(), "kind": "oracle",
+            "cores": used, "kind": "oracle",
             "sample": f"{reps} full step(s) of the workload (M_eo then M_eo^dag, FP64, "
-                      f"32^3x64), {dt:.2f} s each"}
+                      f"{'x'.join(map(str, DIMS))}), {dt:.2f} s each",
+            "single_thread": {"value": round(2 * FLOP_PER_SITE * np.prod(sd) / dt1 / 1e9, 3),
+                              "sample": f"one step on the first {sd[3]} time slices "
+                                        f"({'x'.join(map(str, sd))}, periodic), {dt1:.2f} s"},
+            "cpu_model": cpu_model()}
+
+
+# wall-clock budget of a whole reference-arm run (warm-up plus timed steps)
+REFERENCE_BUDGET_S = 150.0
 
 
 def run_reference(args, rank, world, local):
-    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle, timed on the host cores. Each step is
+    M_eo then M_eo^dag on the workload's first T time slices (a periodic
+    sub-lattice with the same per-site work), T chosen so that warm-up plus
+    K steps stay within a few minutes; T = 64 is the whole workload."""
     if rank != 0:
         return
     import oracle
 
     U, psi = fields()
-    V = int(np.prod(DIMS))
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
-    for _ in range(min(1, args.warmup)):
-        yv = oracle.meo(U, KAPPA, psi, DIMS)
-        oracle.meo_dag(U, KAPPA, yv, DIMS)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        yv = oracle.meo(U, KAPPA, psi, DIMS)
-        oracle.meo_dag(U, KAPPA, yv, DIMS)
-    dt = (time.perf_counter() - t0) / args.steps
+    lt = DIMS[3]
+    # size the sample from one 2-slice step (it doubles as the first warm-up)
+    Us, ps, sd = slab(U, psi, 2)
+    per_slice = oracle_step_seconds(Us, ps, sd, 1) / 2
+    n_steps = args.steps + max(1, args.warmup)
+    T = int(REFERENCE_BUDGET_S / max(n_steps * per_slice, 1e-9))
+    T = max(2, min(lt, T - T % 2))
+    Us, ps, sd = slab(U, psi, T)
+    for _ in range(max(1, args.warmup) - 1):
+        oracle_step_seconds(Us, ps, sd, 1)
+    dt = oracle_step_seconds(Us, ps, sd, args.steps)
+    V = int(np.prod(sd))
     value = 2 * FLOP_PER_SITE * V / dt / 1e9
+    sample = (f"each step: M_eo then M_eo^dag (FP64) on the first {T} of {lt} time slices of the "
+              f"workload ({'x'.join(map(str, sd))}, periodic in t), {dt:.3f} s")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GFlop/s",
-           "n_gpus": world, "steps": args.steps, "warmup": min(1, args.warmup),
+           "n_gpus": world, "steps": args.steps, "warmup": max(1, args.warmup),
            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA},
-           "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s", "cores": threads,
-                            "kind": "oracle",
-                            "sample": "full workload step (M_eo then M_eo^dag, FP64, 32^3x64)"},
+           "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA,
+                      "sample_lattice": list(sd)},
+           "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s",
+                            "cores": oracle.get_threads(), "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": round(value, 3), "unit": "GFlop/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

@@ -337,6 +337,16 @@ int wilson_eo_profile_read(wilson_eo_t h, int max_kernels, char *names, int name
 int wilson_eo_apply_noalloc(const int dims[4], double kappa, const void *gauge, void *out_e,
                             const void *in_e, int dag, void *stream);
 
+/* Measured arithmetic peak of the current GPU in flop/s (2 per fused
+ * multiply-add) for prec WEO_F64 or WEO_F32, written to *flops_per_s. A
+ * measurement aid with no counterpart in the paper: the FP64 hopping kernels
+ * are bound by the FP64 FMA rate rather than by memory on GPUs whose FP64 rate
+ * is a small fraction of their FP32 rate, and their roofline is taken against
+ * this number. Runs a short calibration launch, then ~100 ms of independent
+ * FMA chains on every SM, on `stream`; synchronises with the stream before it
+ * returns. Other precisions: WEO_ERR_ARG. */
+int wilson_eo_alu_peak(int prec, double *flops_per_s, void *stream);
+
 /* Release everything the handle owns (synchronises the device first).
  * NULL is accepted. */
 void wilson_eo_destroy(wilson_eo_t h);

@@ -96,6 +96,7 @@ def _load():
         "wilson_eo_inject_fused_timeout": (I, [P, P, P, P]),
         "wilson_eo_get_algorithm": (I, [P, IP, IP, IP]),
         "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
+        "wilson_eo_alu_peak": (I, [I, ctypes.POINTER(D), P]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
         f = getattr(lib, name, None)
@@ -304,6 +305,14 @@ def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=N
     _check(_load().wilson_eo_apply_noalloc(d, float(kappa), _ptr(gauge), _ptr(out_e), _ptr(in_e),
                                            int(bool(dag)), _stream(stream)),
            "wilson_eo_apply_noalloc")
+
+
+def wilson_eo_alu_peak(prec="f64", stream=None):
+    """Measured FMA peak of the current GPU in flop/s, for prec "f64" or "f32"."""
+    out = ctypes.c_double(0.0)
+    _check(_load().wilson_eo_alu_peak(PREC.get(prec, -1), ctypes.byref(out), _stream(stream)),
+           "wilson_eo_alu_peak")
+    return out.value
 
 
 def wilson_eo_solve(h, x_e, b_e, tol=1e-10, maxiter=10000, mixed=True, stream=None,

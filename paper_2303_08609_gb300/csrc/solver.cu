@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <vector>
 
@@ -130,25 +131,57 @@ __device__ __forceinline__ double re_dot(T2 a, T2 b) { return double(a.x) * b.x 
 #define FOR_ELEMENTS(k) \
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
 
-// mode 0: red = Re<a, b>;  mode 1: pAp = Re<a, b>, alpha = rr / pAp.
-// The solver calls mode 1 with a = b = M p: for A = M^dag M, <p, A p> = |M p|^2,
+// FP32 vectors are read as float4 (two complex numbers; n = 12 V/2 is even and
+// every right-hand side starts on a 16-byte boundary). Squares are summed in
+// FP32 over the handful of values one thread has in flight and only those
+// group sums are accumulated in FP64: per-element FP64 arithmetic would run at
+// the FP64 rate, a small fraction of the FP32 one, and would bound these
+// otherwise memory-bound kernels.
+__device__ __forceinline__ float sq4(float4 q) { return q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w; }
+
+__device__ __forceinline__ long long grid_stride() { return (long long)gridDim.x * blockDim.x; }
+__device__ __forceinline__ long long grid_index() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
+
+// sum of |a_k|^2 over n complex values, this thread's share
+template <typename T2>
+__device__ __forceinline__ double sum_sq(const T2 *a, long long n)
+{
+    double v = 0.0;
+    if constexpr (std::is_same<T2, float2>::value) {
+        const float4 *a4 = reinterpret_cast<const float4 *>(a);
+        const long long n4 = n >> 1, st = grid_stride();
+        long long k = grid_index();
+        for (; k + 3 * st < n4; k += 4 * st) {
+            const float4 q0 = a4[k], q1 = a4[k + st], q2 = a4[k + 2 * st], q3 = a4[k + 3 * st];
+            v += double((sq4(q0) + sq4(q1)) + (sq4(q2) + sq4(q3)));
+        }
+        for (; k < n4; k += st) v += double(sq4(a4[k]));
+    } else {
+        FOR_ELEMENTS(k) v += re_dot(a[k], a[k]);
+    }
+    return v;
+}
+
+// mode 0: red = |a|^2 (every right-hand side);  mode 1: rr = |a|^2 (active
+// ones);  mode 2: pAp = |a|^2 and alpha = rr / pAp (active, finite ones).
+// The solver calls mode 2 with a = M p: for A = M^dag M, <p, A p> = |M p|^2,
 // which reads one vector instead of two and cannot come out negative when the
 // low-precision M and M^dag are not exact adjoints of each other.
 template <typename T2>
-__global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, long long n,
-                                                     SolveScalars *scs, int mode)
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n, SolveScalars *scs,
+                                                       int mode)
 {
     SolveScalars *sc = scs + blockIdx.y;
-    if (!sc->active || (mode == 1 && sc->nonfinite)) return;
-    a += blockIdx.y * n;
-    b += blockIdx.y * n;
-    double v = 0.0;
-    FOR_ELEMENTS(k) v += re_dot(a[k], b[k]);
-    v = block_sum(v);
+    if (mode >= 1 && !sc->active) return;
+    if (mode == 2 && sc->nonfinite) return;
+    double v = block_sum(sum_sq(a + blockIdx.y * n, n));
     double tot;
     if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
         if (mode == 0) {
             sc->red = tot;
+        } else if (mode == 1) {
+            sc->rr = tot;
+            if (!isfinite(tot)) sc->nonfinite = 1;
         } else {
             sc->pAp = tot;
             const double alpha = sc->rr / tot;
@@ -158,23 +191,12 @@ __global__ void __launch_bounds__(kRedThreads) k_dot(const T2 *a, const T2 *b, l
     }
 }
 
-// mode 0: red = |a|^2 (every right-hand side);  mode 1: rr = |a|^2 (active ones)
-template <typename T2>
-__global__ void __launch_bounds__(kRedThreads) k_norm2(const T2 *a, long long n, SolveScalars *scs,
-                                                       int mode)
+__device__ __forceinline__ void axpy4(float4 &y, float a, float4 x)
 {
-    SolveScalars *sc = scs + blockIdx.y;
-    if (mode == 1 && !sc->active) return;
-    a += blockIdx.y * n;
-    double v = 0.0;
-    FOR_ELEMENTS(k) v += re_dot(a[k], a[k]);
-    v = block_sum(v);
-    double tot;
-    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) {
-        if (mode == 0) sc->red = tot;
-        else sc->rr = tot;
-        if (!isfinite(tot)) sc->nonfinite = 1;
-    }
+    y.x += a * x.x;
+    y.y += a * x.y;
+    y.z += a * x.z;
+    y.w += a * x.w;
 }
 
 // x += alpha p ; r -= alpha Ap ; rr_new = |r|^2 ; beta = rr_new / rr ; rr = rr_new
@@ -192,16 +214,44 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
     Ap += o;
     const T alpha = T(sc->alpha);
     double v = 0.0;
-    FOR_ELEMENTS(k) {
-        T2 xv = x[k], rv = r[k];
-        const T2 pv = p[k], av = Ap[k];
-        xv.x += alpha * pv.x;
-        xv.y += alpha * pv.y;
-        rv.x -= alpha * av.x;
-        rv.y -= alpha * av.y;
-        x[k] = xv;
-        r[k] = rv;
-        v += re_dot(rv, rv);
+    if constexpr (std::is_same<T2, float2>::value) {
+        float4 *x4 = reinterpret_cast<float4 *>(x), *r4 = reinterpret_cast<float4 *>(r);
+        const float4 *p4 = reinterpret_cast<const float4 *>(p), *a4 = reinterpret_cast<const float4 *>(Ap);
+        const long long n4 = n >> 1, st = grid_stride();
+        long long k = grid_index();
+        for (; k + st < n4; k += 2 * st) {
+            float4 x0 = x4[k], x1 = x4[k + st], r0 = r4[k], r1 = r4[k + st];
+            const float4 p0 = p4[k], p1 = p4[k + st], a0 = a4[k], a1 = a4[k + st];
+            axpy4(x0, alpha, p0);
+            axpy4(x1, alpha, p1);
+            axpy4(r0, -alpha, a0);
+            axpy4(r1, -alpha, a1);
+            x4[k] = x0;
+            x4[k + st] = x1;
+            r4[k] = r0;
+            r4[k + st] = r1;
+            v += double(sq4(r0) + sq4(r1));
+        }
+        if (k < n4) {
+            float4 x0 = x4[k], r0 = r4[k];
+            axpy4(x0, alpha, p4[k]);
+            axpy4(r0, -alpha, a4[k]);
+            x4[k] = x0;
+            r4[k] = r0;
+            v += double(sq4(r0));
+        }
+    } else {
+        FOR_ELEMENTS(k) {
+            T2 xv = x[k], rv = r[k];
+            const T2 pv = p[k], av = Ap[k];
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            rv.x -= alpha * av.x;
+            rv.y -= alpha * av.y;
+            x[k] = xv;
+            r[k] = rv;
+            v += re_dot(rv, rv);
+        }
     }
     v = block_sum(v);
     double tot;
@@ -217,7 +267,7 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
 
 // p = r + beta p
 template <typename T2>
-__global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *scs)
+__global__ void __launch_bounds__(kRedThreads) k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *scs)
 {
     const SolveScalars *sc = scs + blockIdx.y;
     if (!sc->active || sc->nonfinite) return;
@@ -226,12 +276,32 @@ __global__ void k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *sc
     p += o;
     r += o;
     const T beta = T(sc->beta);
-    FOR_ELEMENTS(k) {
-        T2 pv = p[k];
-        const T2 rv = r[k];
-        pv.x = rv.x + beta * pv.x;
-        pv.y = rv.y + beta * pv.y;
-        p[k] = pv;
+    if constexpr (std::is_same<T2, float2>::value) {
+        float4 *p4 = reinterpret_cast<float4 *>(p);
+        const float4 *r4 = reinterpret_cast<const float4 *>(r);
+        const long long n4 = n >> 1, st = grid_stride();
+        long long k = grid_index();
+        for (; k + st < n4; k += 2 * st) {
+            const float4 q0 = p4[k], q1 = p4[k + st];
+            float4 y0 = r4[k], y1 = r4[k + st];
+            axpy4(y0, beta, q0);
+            axpy4(y1, beta, q1);
+            p4[k] = y0;
+            p4[k + st] = y1;
+        }
+        if (k < n4) {
+            float4 y0 = r4[k];
+            axpy4(y0, beta, p4[k]);
+            p4[k] = y0;
+        }
+    } else {
+        FOR_ELEMENTS(k) {
+            T2 pv = p[k];
+            const T2 rv = r[k];
+            pv.x = rv.x + beta * pv.x;
+            pv.y = rv.y + beta * pv.y;
+            p[k] = pv;
+        }
     }
 }
 
@@ -401,13 +471,13 @@ static int cg_iteration(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bo
     SolveScalars *sc = dev_scal(S);
     if (mixed) {
         WEO_TRY(normal_op(h, S, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
-        k_dot<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->t32.ptr, (const float2 *)S->t32.ptr, n, sc, 1);
+        k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->t32.ptr, n, sc, 2);
         k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->rs.ptr,
                                                           (const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc);
         k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->p.ptr, (const float2 *)S->rs.ptr, n, sc);
     } else {
         WEO_TRY(normal_op(h, S, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
-        k_dot<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->e64.ptr, (const double2 *)S->e64.ptr, n, sc, 1);
+        k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->e64.ptr, n, sc, 2);
         k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->r64.ptr,
                                                            (const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
         k_cg_dir<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->p64.ptr, (const double2 *)S->r64.ptr, n, sc);
@@ -608,6 +678,9 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
                 }
                 const double rr = S->host[r].rr;
                 if (sqrt(rr) < S->delta * r_max[r] || rr <= target[r]) update = true;
+                // an iterated residual far above the last true one: check the
+                // true residual now rather than after the iteration has run away
+                if (rr > kDivergence * kDivergence * rr_min[r]) update = true;
             }
             if (!update) continue;
             // reliable update of every system: fold the increments into x and

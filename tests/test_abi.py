@@ -99,3 +99,11 @@ def test_noalloc_rejects_bad_arguments_before_the_device(lib):
     with pytest.raises(weo.WilsonEOError) as e:
         weo.wilson_eo_apply_noalloc((64, 64, 64, 64), 0.1, z, z.copy(), z)
     assert e.value.status == -2 and "349525" in weo.wilson_eo_last_error()
+
+
+def test_alu_peak_rejects_other_precisions(lib):
+    import paper_2303_08609_gb300 as weo
+
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_alu_peak("f16")
+    assert e.value.status == -1
