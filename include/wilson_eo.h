@@ -236,9 +236,9 @@ int wilson_eo_apply_batch_rhs(int n, const wilson_eo_t *hs, void *const *outs,
 /* Autotune M_eo on this handle with nrhs right-hand sides: every candidate is
  * timed with CUDA events on `stream` and the fastest is kept -- the two-launch
  * algorithm with threads 64/128/192/256 per CTA and 1, 2 or 4 right-hand sides
- * per thread (FP32 handles), and for FP32 / 16-bit handles the fused algorithm
- * with rings of 4, 8, 16 t-slices and 128 / 256 threads (wilson_eo_get_launch,
- * wilson_eo_get_algorithm). threads_out / rhs_block_out describe the winner. Results
+ * per thread or 2 on neighbouring lanes (FP32 / 16-bit handles, nrhs >= 2), and
+ * for FP32 / 16-bit handles the fused algorithm with a lookahead of 4 or 8
+ * t-slices and 128 / 256 threads (wilson_eo_get_launch, wilson_eo_get_algorithm). threads_out / rhs_block_out describe the winner. Results
  * are cached per process by (GPU, extents, precision, link format, nrhs) and,
  * if the environment variable WILSON_EO_TUNE_CACHE names a file, appended to it
  * and read back by later processes. Allocates two temporary spinor fields.
@@ -250,16 +250,18 @@ int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out
  * (apply, apply_dag, force, and the inner operator of the mixed solver):
  *   algo 0  two hop launches with the odd-site intermediate in HBM (default);
  *   algo 1  one persistent launch for both hops of Eq. 4: CTAs take (hop,
- *           t-slice, chunk) items in wavefront order and keep the odd-site
- *           intermediate in a ring of `ring` t-slices (3..64; 0 keeps the
- *           current value, default 8) that stays in L2; `threads` per CTA
- *           128 or 256 (0 keeps the current value). FP32 spinors and
- *           arithmetic; links in the handle's precision.
+ *           t-slice, chunk) items from a queue in which the first hop H_oe
+ *           runs `lookahead` t-slices ahead of the second (1..64, clamped to
+ *           Lt-1; 0 keeps the current value, default 8), so the second hop
+ *           finds the links and the odd-site intermediate of its slices still
+ *           in L2; `threads` per CTA 128 or 256 (0 keeps the current value).
+ *           Same arithmetic and intermediate format as algo 0, so the
+ *           results are bitwise equal.
  * Items wait for the items they depend on with bounded polling; if a wait ever
  * gives up (about a second without progress), the kernel records an error
  * that wilson_eo_check reports as WEO_ERR_TIMEOUT. FP64 handles: algo 1 gives
  * WEO_ERR_UNSUPPORTED. */
-int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads);
+int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads);
 
 /* Failure-path test of the fused kernel: runs one fused M_eo in which the
  * first-hop items never publish their completion (a flag that nothing sets) and
@@ -269,8 +271,8 @@ int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads);
  * hangs; the context stays usable. FP32 / 16-bit handles, device arrays. */
 int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e, void *stream);
 
-/* Current algorithm (0 two launches, 1 fused), fused ring size and threads. */
-int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *ring, int *threads);
+/* Current algorithm (0 two launches, 1 fused), fused lookahead and threads. */
+int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *lookahead, int *threads);
 
 /* Wait for `stream` and report whether any fused launch of this handle since
  * the previous check gave up a bounded wait (WEO_ERR_TIMEOUT: the outputs of
@@ -302,6 +304,15 @@ int wilson_eo_hop_split(wilson_eo_t h, int ranks, int out_parity, int dag, void 
  * while that part is still in L2; order 0: both hops walk upward.
  * wilson_eo_tune sets threads and rhs_block from measurements. */
 int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order);
+
+/* Right-hand sides on neighbouring lanes (FP32 and 16-bit handles): with
+ * lanes = 2, 4 or 8, that many consecutive threads of a CTA take the same site
+ * and different right-hand sides of a multi-RHS apply, so each link is fetched
+ * once per warp for all of them while every thread keeps one right-hand side's
+ * registers. Used when rhs_block is 1; clamped to nrhs. lanes = 1 (default)
+ * turns it off. WEO_ERR_ARG for other values, WEO_ERR_UNSUPPORTED for lanes > 1
+ * on an FP64 handle. */
+int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes);
 
 /* Per-kernel timing. With profiling on, every kernel the handle launches is
  * bracketed by two CUDA events on its stream (a few microseconds of host time

@@ -97,6 +97,7 @@ def _load():
         "wilson_eo_get_algorithm": (I, [P, IP, IP, IP]),
         "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
         "wilson_eo_alu_peak": (I, [I, ctypes.POINTER(D), P]),
+        "wilson_eo_set_rhs_lanes": (I, [P, I]),
     }
     for name, (res, args) in list(sig.items()) + list(optional.items()):
         f = getattr(lib, name, None)
@@ -307,6 +308,12 @@ def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=N
            "wilson_eo_apply_noalloc")
 
 
+def wilson_eo_set_rhs_lanes(h, lanes):
+    """Right-hand sides of a multi-RHS apply on ``lanes`` neighbouring threads per
+    site (1, 2, 4 or 8), sharing each link load."""
+    _check(_load().wilson_eo_set_rhs_lanes(h, int(lanes)), "wilson_eo_set_rhs_lanes")
+
+
 def wilson_eo_alu_peak(prec="f64", stream=None):
     """Measured FMA peak of the current GPU in flop/s, for prec "f64" or "f32"."""
     out = ctypes.c_double(0.0)
@@ -425,10 +432,11 @@ def wilson_eo_tune(h, nrhs=1, stream=None):
     return t.value, r.value, ms.value
 
 
-def wilson_eo_set_algorithm(h, algo, ring=0, threads=0):
-    """algo 0: two hop launches; 1: fused single launch with an L2 ring of t-slices."""
+def wilson_eo_set_algorithm(h, algo, lookahead=0, threads=0):
+    """algo 0: two hop launches; 1: fused single launch, the first hop running
+    ``lookahead`` t-slices ahead of the second."""
     a = {"two_pass": 0, "fused": 1}.get(algo, algo)
-    _check(_load().wilson_eo_set_algorithm(h, int(a), int(ring), int(threads)),
+    _check(_load().wilson_eo_set_algorithm(h, int(a), int(lookahead), int(threads)),
            "wilson_eo_set_algorithm")
 
 
@@ -436,7 +444,7 @@ def wilson_eo_get_algorithm(h):
     a, r, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_load().wilson_eo_get_algorithm(h, ctypes.byref(a), ctypes.byref(r), ctypes.byref(t)),
            "wilson_eo_get_algorithm")
-    return {"algo": a.value, "ring": r.value, "threads": t.value}
+    return {"algo": a.value, "lookahead": r.value, "threads": t.value}
 
 
 def wilson_eo_hop_split(h, ranks, out_parity, dag, out, inp, stream=None):

@@ -163,8 +163,9 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
     const int prec = g.prec;
     if (h->algo == 1 && prec != WEO_F64) {
         const long long ext32 = h->vh * 96;
+        WEO_TRY(tmp.ensure((size_t)h->vh * (prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16))));
         for (int r = 0; r < nrhs; ++r)
-            WEO_TRY(meo_fused(h, g, static_cast<char *>(out) + r * ext32,
+            WEO_TRY(meo_fused(h, g, tmp.ptr, static_cast<char *>(out) + r * ext32,
                               static_cast<const char *>(in) + r * ext32, dag, s));
         return WEO_OK;
     }
@@ -325,17 +326,29 @@ int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order)
     return WEO_OK;
 }
 
-int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int ring, int threads)
+int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8)
+        return set_error(WEO_ERR_ARG, "lanes must be 1, 2, 4 or 8");
+    if (lanes != 1 && h->prec == WEO_F64)
+        return set_error(WEO_ERR_UNSUPPORTED, "lanes > 1 needs an FP32 or 16-bit handle");
+    h->cfg[h->prec].lanes = lanes;
+    return WEO_OK;
+}
+
+int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
     if (algo != 0 && algo != 1) return set_error(WEO_ERR_ARG, "algo must be 0 (two launches) or 1 (fused)");
     if (algo == 1 && h->prec == WEO_F64)
         return set_error(WEO_ERR_UNSUPPORTED, "the fused M_eo has FP32 arithmetic only");
-    if (ring != 0 && (ring < 3 || ring > 64)) return set_error(WEO_ERR_ARG, "ring must be 0 or in 3..64");
+    if (lookahead != 0 && (lookahead < 1 || lookahead > 64))
+        return set_error(WEO_ERR_ARG, "lookahead must be 0 or in 1..64");
     if (threads != 0 && threads != 128 && threads != 256)
         return set_error(WEO_ERR_ARG, "threads must be 0, 128 or 256");
     h->algo = algo;
-    if (ring) h->fused_ring = ring;
+    if (lookahead) h->fused_lookahead = lookahead;
     if (threads) h->fused_threads = threads;
     return WEO_OK;
 }
@@ -348,7 +361,8 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
         if (!is_device_pointer(out_e) || !is_device_pointer(in_e))
             return set_error(WEO_ERR_ARG, "device arrays only");
         DeviceGuard dg(h->device);
-        return meo_fused(h, h->gauge, out_e, in_e, false, static_cast<cudaStream_t>(stream), true);
+        WEO_TRY(h->tmp.ensure((size_t)h->vh * (h->prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16))));
+        return meo_fused(h, h->gauge, h->tmp.ptr, out_e, in_e, false, static_cast<cudaStream_t>(stream), true);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_fused_timeout");
     }
@@ -381,7 +395,7 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
     if (device_bytes)
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
-                        h->even1.bytes + h->fused_tmp.bytes + h->fused_ctrl.bytes + h->halo.bytes +
+                        h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes +
                         h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
@@ -634,7 +648,6 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->stage_in.release();
     h->stage_out.release();
     h->stage_aux.release();
-    h->fused_tmp.release();
     h->fused_ctrl.release();
     h->halo.release();
     solver_destroy(h);

@@ -1,92 +1,97 @@
-// Fused M_eo: both hops of Eq. 4 in one persistent kernel, with the odd-site
-// intermediate kept in a small ring of t-slices that stays in L2.
+// Fused M_eo: both hops of Eq. 4 in one persistent launch over a wavefront of
+// t-slices, each site computed by the same per-site code as the two-launch
+// kernels.
 //
-// Work is a queue of items (hop, t-slice, chunk of CTA size). Slice tasks are
-// ordered as a wavefront:
-//     A(Lt-1), A(0), A(1), B(0), A(2), B(1), ..., A(Lt-2), B(Lt-3), B(Lt-2), B(Lt-1)
-// where A(t) = H_oe onto the odd sites of slice t (written to the ring) and
-// B(t) = in - kappa^2 H_eo tmp onto the even sites of slice t (read from the
-// ring slices t-1, t, t+1). CTAs take items from an atomic ticket in queue
-// order. An item may only wait for items earlier in the queue:
-//   B(t) waits until A(t-1), A(t), A(t+1) are complete;
-//   A(t) (ring slot t mod R) waits until the three B tasks that read the
-//        slot's previous slice (t-R) are complete (needs R >= 3).
-// Because a ticket is only handed out after all earlier ones, the earliest
-// unfinished item never waits, so the queue always progresses. Every wait is
-// bounded: after `spin_limit` polls the CTA records an error code and gives up,
-// and every other wait gives up as soon as it sees the error; the host reports
-// WEO_ERR_TIMEOUT.
+// Work is a queue of items (hop, t-slice, CTA-sized chunk). Slice tasks are
+// ordered as a wavefront over t with lookahead D:
+//     A(Lt-1), A(0) .. A(D-1), A(D), B(0), A(D+1), B(1), ..., A(Lt-2), B(Lt-2-D), B(..), .., B(Lt-1)
+// where A(t) = H_oe onto the odd sites of slice t (into the full-size odd
+// intermediate) and B(t) = in - kappa^2 H_eo mid onto the even sites of slice t,
+// which reads the intermediate at slices t-1, t and t+1. CTAs take items from an
+// atomic ticket in queue order; B(t) waits until A(t-1), A(t) and A(t+1) are
+// complete, A items never wait (every slice has its own intermediate storage).
+// A ticket is only handed out after all earlier ones and every wait is for an
+// earlier item, so the earliest unfinished item never waits and the queue
+// always progresses. Every wait is bounded: after `spin_limit` polls the CTA
+// records an error code and gives up, every other wait gives up as soon as it
+// sees the error, and the host reports WEO_ERR_TIMEOUT.
 //
-// Slices 0 and Lt-1 keep dedicated slots (they are read at both ends of the
-// periodic wavefront). The ring is read with L2-only loads (ld.global.cg): its
-// slots are rewritten during the launch, so L1 copies could be stale.
-//
-// DRAM traffic per M_eo approaches the minimum -- the even input once, every
-// link once (A(t) and B(t) read the same slice's links within a short window)
-// and the output once -- instead of two full passes with the intermediate
-// written to and read back from HBM.
+// What this saves against two launches: B(t) runs D slices behind A, so the
+// links of slice t, which A(t) read a few slices earlier, and the intermediate
+// slices A just wrote are still in L2 when B reads them (with D = 1 the B items
+// wait for A(t+1), issued just before them; D = 4..8 leaves no such stalls). DRAM sees the input,
+// the links and the output about once, plus the write-back of the intermediate.
+// The intermediate is read through L2 only (ld.global.cg): it is written during
+// the launch, so a copy held in an SM's L1 could be stale.
 #include <algorithm>
 
 #include "weo_internal.h"
+#include "weo_dslash.cuh"
 
 namespace weo {
 
-struct FusedParams {
-    int lxh, ly, lz, lt;
-    int vs;          // sites of one parity in one t-slice
-    int vh;
-    int chunks;      // CTA-sized chunks per slice
-    int ring;        // ring slots R (>= 3) for slices 1 .. Lt-2
-    int total;       // items in the queue
-    const float2 *in;
-    float2 *out;
-    float2 *tmp;     // (ring + 2) slots of [12][vs] complex64
-    const char *gauge;
-    long long gauge_pb;
-    float a;         // -kappa^2
-    unsigned int *ctrl;  // [0] sticky error (kept across launches), [1] ticket,
-                         // [2] this launch's error, [3 .. 3+Lt) done A, [3+Lt .. 3+2Lt) done B
-    unsigned int spin_limit;
-    int inject;      // test of the failure path: first-hop items never publish completion
+// Intermediate loaders that bypass L1 (same layouts as SpF32 and Sp16).
+struct SpF32L2 : SpF32 {
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const float2 *p = static_cast<const float2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float2 d = __ldcg(p + k * vh + i);
+            v[k] = {R(d.x), R(d.y)};
+        }
+    }
 };
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
+template <class Tr>
+struct Sp16L2 : Sp16<Tr> {
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const uint4 *p = static_cast<const uint4 *>(base);
+        const float n = __ldcg(reinterpret_cast<const float *>(p + 3 * vh) + i);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const uint4 w = __ldcg(p + q * vh + i);
+            const float2 a = Tr::to_f2(w.x), b = Tr::to_f2(w.y), c = Tr::to_f2(w.z), d = Tr::to_f2(w.w);
+            v[4 * q + 0] = {R(a.x * n), R(a.y * n)};
+            v[4 * q + 1] = {R(b.x * n), R(b.y * n)};
+            v[4 * q + 2] = {R(c.x * n), R(c.y * n)};
+            v[4 * q + 3] = {R(d.x * n), R(d.y * n)};
+        }
+    }
+};
+
+struct FusedParams {
+    HopParams a;     // H_oe: in (even) -> mid (odd)
+    HopParams b;     // mid -> out (even), out = in + a * H_eo mid
+    int vs;          // sites of one parity in one t-slice
+    int lt;
+    int lookahead;   // slices the first hop runs ahead of the second (1 .. Lt-1)
+    int chunks;      // CTA-sized chunks per slice
+    int total;       // items in the queue
+    unsigned int *ctrl;  // [0] sticky error (kept across launches), [1] ticket,
+                         // [2] this launch's error, [3 .. 3+Lt) chunks of A(t) done
+    unsigned int spin_limit;
+    int inject;      // test of the failure path: A items never publish completion
+};
+
+__device__ __forceinline__ unsigned int fused_ld_acquire(const unsigned int *p)
 {
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ int ring_slot(const FusedParams &f, int t)
-{
-    return t == 0 ? 0 : (t == f.lt - 1 ? 1 : 2 + t % f.ring);
-}
-
-// slice task k -> (phase B?, t)
-__device__ __forceinline__ void slice_task(const FusedParams &f, int k, bool &phase_b, int &t)
-{
-    const int L = f.lt;
-    if (k == 0) {
-        phase_b = false;
-        t = L - 1;
-    } else if (k == 1) {
-        phase_b = false;
-        t = 0;
-    } else if (k < 2 * (L - 1)) {
-        phase_b = k & 1;
-        t = phase_b ? (k >> 1) - 1 : (k >> 1);
-    } else {
-        phase_b = true;
-        t = k == 2 * (L - 1) ? L - 2 : L - 1;
-    }
-}
-
 // Wait (thread 0) until ctrl[idx] >= target; false on timeout or a prior error.
-__device__ __forceinline__ bool wait_count(const FusedParams &f, int idx, unsigned int target)
+__device__ __forceinline__ bool fused_wait(const FusedParams &f, int idx, unsigned int target)
 {
     unsigned int n = 0;
-    while (ld_acquire(f.ctrl + idx) < target) {
-        if (ld_acquire(f.ctrl + 2) != 0u) return false;
+    while (fused_ld_acquire(f.ctrl + idx) < target) {
+        if (fused_ld_acquire(f.ctrl + 2) != 0u) return false;
         if (++n > f.spin_limit) {
             atomicExch(f.ctrl + 2, 1u);
             atomicOr(f.ctrl + 0, 1u);
@@ -97,100 +102,32 @@ __device__ __forceinline__ bool wait_count(const FusedParams &f, int idx, unsign
     return true;
 }
 
-template <class Lk, int MU, bool FWD, int S0, bool PB>
-__device__ __forceinline__ void fused_dir(cx<float> acc[12], const FusedParams &f, int t_nb,
-                                          long long nb_global, long long link_idx, int link_par)
+// slice task k -> (phase B?, t): A(Lt-1), A(0) .. A(D-1), then A(t+D) and B(t)
+// in turn while t+D <= Lt-2, then the remaining B(t) (D = lookahead >= 1)
+__device__ __forceinline__ void fused_task(int L, int D, int k, bool &phase_b, int &t)
 {
-    constexpr int S = FWD ? S0 : -S0;
-    cx<float> U[3][3];
-    Lk::load(f.gauge + (2 * MU + link_par) * f.gauge_pb, f.vh, link_idx, U);
-    cx<float> v[12];
-    if (PB) {
-        // odd intermediate from the ring slot of slice t_nb, local index
-        const float2 *base = f.tmp + (long long)ring_slot(f, t_nb) * 12 * f.vs;
-        const long long local = nb_global - (long long)t_nb * f.vs;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            float2 d = __ldcg(base + (long long)k * f.vs + local);
-            v[k] = {d.x, d.y};
-        }
-    } else {
-        SpF32::load(f.in, f.vh, nb_global, v);
+    if (k == 0) {
+        phase_b = false;
+        t = L - 1;
+        return;
     }
-    cx<float> h[2][3], w[2][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            cx<float> z = {0.f, 0.f};
-#pragma unroll
-            for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[s][b], z) : cfmaconj(U[b][a], h[s][b], z);
-            w[s][a] = z;
-        }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) reconstruct<MU, S>(acc[c], acc[3 + c], acc[6 + c], acc[9 + c], w[0][c], w[1][c]);
-}
-
-// One site of an A (PB = false: odd output into the ring) or B item (PB = true:
-// even output with the axpy of Eq. 4).
-template <class Lk, bool Dag, bool PB>
-__device__ __forceinline__ void fused_site(const FusedParams &f, int t, int s)
-{
-    constexpr int S0 = Dag ? -1 : 1;
-    const int out_parity = PB ? 0 : 1;
-    const int in_par = out_parity ^ 1;
-    int rem = s;
-    const int xh = rem % f.lxh;
-    rem /= f.lxh;
-    const int y = rem % f.ly;
-    const int z = rem / f.ly;
-    const int par = (y + z + t + out_parity) & 1;
-    const long long i = (long long)t * f.vs + s;
-    const int sy = f.lxh, sz = f.lxh * f.ly;
-    const int row = s - xh;
-    const int xp = par ? (xh + 1 == f.lxh ? 0 : xh + 1) : xh;
-    const int xm = par ? xh : (xh == 0 ? f.lxh - 1 : xh - 1);
-    const long long base = (long long)t * f.vs;
-    const long long n_xp = base + row + xp, n_xm = base + row + xm;
-    const long long n_yp = base + s + (y + 1 == f.ly ? -(f.ly - 1) * sy : sy);
-    const long long n_ym = base + s + (y == 0 ? (f.ly - 1) * sy : -sy);
-    const long long n_zp = base + s + (z + 1 == f.lz ? -(f.lz - 1) * sz : sz);
-    const long long n_zm = base + s + (z == 0 ? (f.lz - 1) * sz : -sz);
-    const int tp = t + 1 == f.lt ? 0 : t + 1, tm = t == 0 ? f.lt - 1 : t - 1;
-    const long long n_tp = (long long)tp * f.vs + s, n_tm = (long long)tm * f.vs + s;
-
-    cx<float> acc[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-    fused_dir<Lk, 0, true, S0, PB>(acc, f, t, n_xp, i, out_parity);
-    fused_dir<Lk, 0, false, S0, PB>(acc, f, t, n_xm, n_xm, in_par);
-    fused_dir<Lk, 1, true, S0, PB>(acc, f, t, n_yp, i, out_parity);
-    fused_dir<Lk, 1, false, S0, PB>(acc, f, t, n_ym, n_ym, in_par);
-    fused_dir<Lk, 2, true, S0, PB>(acc, f, t, n_zp, i, out_parity);
-    fused_dir<Lk, 2, false, S0, PB>(acc, f, t, n_zm, n_zm, in_par);
-    fused_dir<Lk, 3, true, S0, PB>(acc, f, tp, n_tp, i, out_parity);
-    fused_dir<Lk, 3, false, S0, PB>(acc, f, tm, n_tm, n_tm, in_par);
-
-    if (PB) {
-        cx<float> xv[12];
-        SpF32::load(f.in, f.vh, i, xv);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            acc[k].r = fmaf(f.a, acc[k].r, xv[k].r);
-            acc[k].i = fmaf(f.a, acc[k].i, xv[k].i);
-        }
-        SpF32::store(f.out, f.vh, i, acc);
+    if (k <= D) {
+        phase_b = false;
+        t = k - 1;
+        return;
+    }
+    const int kp = k - (D + 1), pairs = L - 1 - D;
+    if (kp < 2 * pairs) {
+        phase_b = kp & 1;
+        t = phase_b ? (kp >> 1) : (kp >> 1) + D;
     } else {
-        float2 *dst = f.tmp + (long long)ring_slot(f, t) * 12 * f.vs;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) __stcg(dst + (long long)k * f.vs + s, make_float2(acc[k].r, acc[k].i));
+        phase_b = true;
+        t = pairs + (kp - 2 * pairs);
     }
 }
 
-template <class Lk, bool Dag, int THREADS>
-__global__ void __launch_bounds__(THREADS) fused_meo_kernel(const FusedParams f)
+template <class SMid, class SMidL2, class Lk, bool Dag, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) fused_meo_kernel(const FusedParams f)
 {
     __shared__ int sh_item;
     __shared__ int sh_ok;
@@ -203,119 +140,145 @@ __global__ void __launch_bounds__(THREADS) fused_meo_kernel(const FusedParams f)
         const int k = q / f.chunks, c = q - k * f.chunks;
         bool pb;
         int t;
-        slice_task(f, k, pb, t);
+        fused_task(L, f.lookahead, k, pb, t);
         if (threadIdx.x == 0) {
             bool ok = true;
-            const unsigned int full = (unsigned int)f.chunks;
             if (pb) {
+                const unsigned int full = (unsigned int)f.chunks;
                 const int tm = t == 0 ? L - 1 : t - 1, tp = t + 1 == L ? 0 : t + 1;
-                ok = wait_count(f, 3 + tm, full) && wait_count(f, 3 + t, full) &&
-                     wait_count(f, 3 + tp, full);
-            } else if (t >= 1 && t <= L - 2 && t - f.ring >= 1) {
-                const int prev = t - f.ring;  // previous slice in this ring slot
-                ok = wait_count(f, 3 + L + prev - 1, full) && wait_count(f, 3 + L + prev, full) &&
-                     wait_count(f, 3 + L + prev + 1, full);
+                ok = fused_wait(f, 3 + tm, full) && fused_wait(f, 3 + t, full) && fused_wait(f, 3 + tp, full);
             }
             sh_ok = ok;
         }
         __syncthreads();
         if (!sh_ok) break;  // give up after a recorded error
-        const int s = c * THREADS + threadIdx.x;
+        const int s = c * THREADS + (int)threadIdx.x;
         if (s < f.vs) {
-            if (pb) fused_site<Lk, Dag, true>(f, t, s);
-            else fused_site<Lk, Dag, false>(f, t, s);
+            const int i = t * f.vs + s;
+            if (pb) hop_site<SMidL2, SpF32, SpF32, Lk, Dag, true, 1>(f.b, i, 0);
+            else hop_site<SpF32, SMid, SpF32, Lk, Dag, false, 1>(f.a, i, 0);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && !(f.inject && !pb)) {
+        if (threadIdx.x == 0 && !pb && !f.inject) {
             __threadfence();
-            atomicAdd(f.ctrl + 3 + (pb ? L : 0) + t, 1u);
+            atomicAdd(f.ctrl + 3 + t, 1u);
         }
     }
 }
 
-template <class Lk, bool Dag>
-static int launch_fused_t(const FusedParams &f0, int threads, cudaStream_t s)
+template <class SMid, class SMidL2, class Lk, bool Dag, int THREADS, int MINB>
+static int launch_fused_v(FusedParams f, int sms, cudaStream_t s)
 {
-    FusedParams f = f0;
-    f.chunks = (f.vs + threads - 1) / threads;
+    int per_sm = 0;
+    auto kern = fused_meo_kernel<SMid, SMidL2, Lk, Dag, THREADS, MINB>;
+    f.chunks = (f.vs + THREADS - 1) / THREADS;
     f.total = 2 * f.lt * f.chunks;
-    int dev = 0, sms = 0, per_sm = 0;
-    WEO_CUDA(cudaGetDevice(&dev));
-    WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (threads == 256) {
-        WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_meo_kernel<Lk, Dag, 256>, 256, 0));
-        fused_meo_kernel<Lk, Dag, 256><<<sms * per_sm, 256, 0, s>>>(f);
-    } else {
-        WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_meo_kernel<Lk, Dag, 128>, 128, 0));
-        fused_meo_kernel<Lk, Dag, 128><<<sms * per_sm, 128, 0, s>>>(f);
-    }
+    WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
+    if (per_sm < 1) return set_error(WEO_ERR_CUDA, "fused kernel cannot be resident");
+    kern<<<sms * per_sm, THREADS, 0, s>>>(f);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
 
-template <class Lk>
-static int launch_fused_d(const FusedParams &f, bool dag, int threads, cudaStream_t s)
+// 128 threads with six CTAs per SM (85 registers) or 256 threads with three:
+// both measured faster than the 64-register cap of the two-launch kernels,
+// which makes this kernel (both hops' code in one body) spill heavily.
+template <class SMid, class SMidL2, class Lk, bool Dag>
+static int launch_fused_t(FusedParams f, int threads, cudaStream_t s)
 {
-    return dag ? launch_fused_t<Lk, true>(f, threads, s) : launch_fused_t<Lk, false>(f, threads, s);
+    int dev = 0, sms = 0;
+    WEO_CUDA(cudaGetDevice(&dev));
+    WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (threads == 256) return launch_fused_v<SMid, SMidL2, Lk, Dag, 256, 3>(f, sms, s);
+    return launch_fused_v<SMid, SMidL2, Lk, Dag, 128, 6>(f, sms, s);
 }
 
-// Size the ring and control words (outside any stream capture).
+template <class SMid, class SMidL2, class Lk>
+static int launch_fused_d(const FusedParams &f, bool dag, int threads, cudaStream_t s)
+{
+    return dag ? launch_fused_t<SMid, SMidL2, Lk, true>(f, threads, s)
+               : launch_fused_t<SMid, SMidL2, Lk, false>(f, threads, s);
+}
+
+// M_eo (or M_eo^dag) of one right-hand side with FP32 spinors through the
+// fused kernel, links from `g` (FP32 with an FP32 intermediate, or FP16 /
+// BF16 with a 16-bit intermediate as in the two-launch path). `mid` holds the
+// odd intermediate (96 or 52 bytes per odd site).
+int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, const void *in, bool dag,
+              cudaStream_t s, bool inject_timeout)
+{
+    if (g.prec == WEO_F64) return set_error(WEO_ERR_UNSUPPORTED, "the fused M_eo has FP32 arithmetic only");
+    const int L = h->dims[3];
+    WEO_TRY(fused_prepare(h, s));
+    const size_t nctrl = (size_t)(3 + L);
+    // reset the ticket, this launch's error and the completion counters
+    WEO_CUDA(cudaMemsetAsync(static_cast<unsigned int *>(h->fused_ctrl.ptr) + 1, 0,
+                             (nctrl - 1) * sizeof(unsigned int), s));
+    FusedParams f;
+    HopParams p = geom_params(h);
+    p.nrhs = 1;
+    p.gauge = static_cast<const char *>(g.buf.ptr);
+    p.gauge_pb = g.pb;
+    const long long ext = h->vh * 96;
+    const long long mid_ext = h->vh * (g.prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16));
+    p.reverse = 0;
+    p.out_parity = 1;
+    p.in = in;
+    p.in_stride = ext;
+    p.out = mid;
+    p.out_stride = mid_ext;
+    p.x = nullptr;
+    p.x_stride = 0;
+    p.a = 0.0;
+    f.a = p;
+    p.out_parity = 0;
+    p.in = mid;
+    p.in_stride = mid_ext;
+    p.out = out;
+    p.out_stride = ext;
+    p.x = in;
+    p.x_stride = ext;
+    p.a = -h->kappa * h->kappa;
+    f.b = p;
+    f.vs = (h->dims[0] / 2) * h->dims[1] * h->dims[2];
+    f.lt = L;
+    f.lookahead = std::max(1, std::min(h->fused_lookahead, L - 1));
+    f.chunks = f.total = 0;
+    f.ctrl = static_cast<unsigned int *>(h->fused_ctrl.ptr);
+    f.spin_limit = 1u << 24;  // at least ~1 s of polling (64 ns sleeps) before giving up
+    f.inject = inject_timeout ? 1 : 0;
+    if (inject_timeout) f.spin_limit = 1u << 12;  // give up after ~0.3 ms
+    const int threads = h->fused_threads == 256 ? 256 : 128;
+    const bool c = g.fmt == WEO_LINK12;
+    int tok = prof_begin(h, kernel_label("fused", g.prec, g.fmt, dag, true).c_str(), s);
+    int st;
+    switch (g.prec) {
+    case WEO_F32:
+        st = c ? launch_fused_d<SpF32, SpF32L2, LkF32_12>(f, dag, threads, s)
+               : launch_fused_d<SpF32, SpF32L2, LkF32_18>(f, dag, threads, s);
+        break;
+    case WEO_F16:
+        st = c ? launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_12>(f, dag, threads, s)
+               : launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_18>(f, dag, threads, s);
+        break;
+    default:
+        st = c ? launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_12>(f, dag, threads, s)
+               : launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_18>(f, dag, threads, s);
+        break;
+    }
+    prof_end(h, tok, s);
+    return st;
+}
+
+// Control words (outside any stream capture).
 int fused_prepare(wilson_eo_s *h, cudaStream_t s)
 {
-    const int L = h->dims[3];
-    const long long vs = (long long)(h->dims[0] / 2) * h->dims[1] * h->dims[2];
-    const int ring = std::max(3, h->fused_ring);
-    WEO_TRY(h->fused_tmp.ensure((size_t)(2 + ring) * 12 * vs * sizeof(float2)));
-    const size_t nctrl = (size_t)(3 + 2 * L);
+    const size_t nctrl = (size_t)(3 + h->dims[3]);
     if (!h->fused_ctrl.ptr || h->fused_ctrl.bytes < nctrl * sizeof(unsigned int)) {
         WEO_TRY(h->fused_ctrl.ensure(nctrl * sizeof(unsigned int)));
         WEO_CUDA(cudaMemsetAsync(h->fused_ctrl.ptr, 0, nctrl * sizeof(unsigned int), s));
     }
     return WEO_OK;
-}
-
-// M_eo (or M_eo^dag) with FP32 spinors through the fused kernel, links from `g`
-// (FP32, FP16 or BF16; 18 or 12 reals).
-int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, bool dag,
-              cudaStream_t s, bool inject_timeout)
-{
-    if (g.prec == WEO_F64) return set_error(WEO_ERR_UNSUPPORTED, "the fused kernel has FP32 arithmetic only");
-    const int L = h->dims[3];
-    FusedParams f;
-    f.lxh = h->dims[0] / 2;
-    f.ly = h->dims[1];
-    f.lz = h->dims[2];
-    f.lt = L;
-    f.vs = f.lxh * f.ly * f.lz;
-    f.vh = (int)h->vh;
-    f.ring = std::max(3, h->fused_ring);
-    const int threads = h->fused_threads == 256 ? 256 : 128;
-    WEO_TRY(fused_prepare(h, s));
-    const size_t nctrl = (size_t)(3 + 2 * L);
-    // reset the ticket, this launch's error and the completion counters
-    WEO_CUDA(cudaMemsetAsync(static_cast<unsigned int *>(h->fused_ctrl.ptr) + 1, 0,
-                             (nctrl - 1) * sizeof(unsigned int), s));
-    f.in = static_cast<const float2 *>(in);
-    f.out = static_cast<float2 *>(out);
-    f.tmp = static_cast<float2 *>(h->fused_tmp.ptr);
-    f.gauge = static_cast<const char *>(g.buf.ptr);
-    f.gauge_pb = g.pb;
-    f.a = (float)(-h->kappa * h->kappa);
-    f.ctrl = static_cast<unsigned int *>(h->fused_ctrl.ptr);
-    f.spin_limit = 1u << 24;  // at least ~1 s of polling (64 ns sleeps) before giving up
-    f.inject = inject_timeout ? 1 : 0;
-    if (inject_timeout) f.spin_limit = 1u << 12;  // give up after ~0.3 ms
-    f.chunks = f.total = 0;
-    const bool c = g.fmt == WEO_LINK12;
-    int tok = prof_begin(h, kernel_label("fused", g.prec, g.fmt, dag, true).c_str(), s);
-    int st;
-    switch (g.prec) {
-    case WEO_F32: st = c ? launch_fused_d<LkF32_12>(f, dag, threads, s) : launch_fused_d<LkF32_18>(f, dag, threads, s); break;
-    case WEO_F16: st = c ? launch_fused_d<LkH16_12>(f, dag, threads, s) : launch_fused_d<LkH16_18>(f, dag, threads, s); break;
-    default: st = c ? launch_fused_d<LkB16_12>(f, dag, threads, s) : launch_fused_d<LkB16_18>(f, dag, threads, s); break;
-    }
-    prof_end(h, tok, s);
-    return st;
 }
 
 // Sticky error word of the fused kernel (set when a bounded wait gave up):

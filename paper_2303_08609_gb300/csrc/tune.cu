@@ -1,11 +1,13 @@
 // Autotuner for M_eo: times each candidate on the handle's own lattice and
 // keeps the fastest. Candidates: the two-launch algorithm with 64..256 threads
-// per CTA and (FP32 handles) 1, 2 or 4 right-hand sides per thread; and, for
-// FP32 / 16-bit handles, the fused single-launch algorithm with rings of 4, 8
-// or 16 t-slices and 128 or 256 threads per CTA. Results are cached per
-// process, keyed by (GPU name, extents, precision, link format, nrhs), and
-// optionally in a text file named by the environment variable
-// WILSON_EO_TUNE_CACHE (one "v2 key algo threads rhs_block ring ms" line each).
+// per CTA and (FP32 / 16-bit handles with several right-hand sides) 1, 2 or 4
+// right-hand sides per thread, or two right-hand sides on neighbouring lanes;
+// and, for FP32 / 16-bit handles, the fused single-launch algorithm with a
+// lookahead of 4 or 8 t-slices and 128 or 256 threads per CTA. Results are
+// cached per process, keyed by (GPU name, extents, precision, link format,
+// nrhs), and optionally in a text file named by the environment variable
+// WILSON_EO_TUNE_CACHE (one "v3 key algo threads rhs_block lanes lookahead ms"
+// line each).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -21,7 +23,7 @@
 namespace weo {
 
 struct TuneEntry {
-    int algo, threads, rhs_block, ring;
+    int algo, threads, rhs_block, lanes, lookahead;
     double ms;
 };
 
@@ -57,9 +59,9 @@ static void load_tune_file()
     if (!f) return;
     char tag[8], key[400];
     TuneEntry e;
-    while (fscanf(f, "%7s %399s %d %d %d %d %lf", tag, key, &e.algo, &e.threads, &e.rhs_block,
-                  &e.ring, &e.ms) == 7)
-        if (strcmp(tag, "v2") == 0) g_tune_cache[key] = e;
+    while (fscanf(f, "%7s %399s %d %d %d %d %d %lf", tag, key, &e.algo, &e.threads, &e.rhs_block,
+                  &e.lanes, &e.lookahead, &e.ms) == 8)
+        if (strcmp(tag, "v3") == 0) g_tune_cache[key] = e;
     fclose(f);
 }
 
@@ -69,8 +71,22 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "v2 %s %d %d %d %d %.6f\n", key.c_str(), e.algo, e.threads, e.rhs_block, e.ring, e.ms);
+    fprintf(f, "v3 %s %d %d %d %d %d %.6f\n", key.c_str(), e.algo, e.threads, e.rhs_block, e.lanes,
+            e.lookahead, e.ms);
     fclose(f);
+}
+
+static void apply_entry(wilson_eo_s *h, const TuneEntry &e)
+{
+    h->algo = e.algo;
+    if (e.algo == 1) {
+        h->fused_threads = e.threads;
+        h->fused_lookahead = e.lookahead;
+    } else {
+        h->cfg[h->prec].threads = e.threads;
+        h->cfg[h->prec].rhs_block = e.rhs_block;
+        h->cfg[h->prec].lanes = e.lanes;
+    }
 }
 
 int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int *rhs_out,
@@ -83,14 +99,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             const TuneEntry &e = it->second;
-            h->algo = e.algo;
-            if (e.algo == 1) {
-                h->fused_threads = e.threads;
-                h->fused_ring = e.ring;
-            } else {
-                h->cfg[h->prec].threads = e.threads;
-                h->cfg[h->prec].rhs_block = e.rhs_block;
-            }
+            apply_entry(h, e);
             if (threads_out) *threads_out = e.threads;
             if (rhs_out) *rhs_out = e.rhs_block;
             if (ms_out) *ms_out = e.ms;
@@ -116,28 +125,20 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         if (nrhs >= 4) rb.push_back(4);
     }
     const LaunchCfg saved = h->cfg[h->prec];
-    const int saved_algo = h->algo, saved_ring = h->fused_ring, saved_fthreads = h->fused_threads;
+    const int saved_algo = h->algo, saved_la = h->fused_lookahead, saved_fthreads = h->fused_threads;
     Profiler *saved_prof = h->prof;
     h->prof = nullptr;
-    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved_ring, 1e30};
-    struct Cand {
-        int algo, threads, rb, ring;
-    };
-    std::vector<Cand> cands;
-    for (int threads : {64, 128, 192, 256})
-        for (int r : rb) cands.push_back({0, threads, r, 0});
+    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30};
+    std::vector<TuneEntry> cands;
+    for (int threads : {64, 128, 192, 256}) {
+        for (int r : rb) cands.push_back({0, threads, r, 1, 0, 0.0});
+        if (h->prec != WEO_F64 && nrhs >= 2) cands.push_back({0, threads, 1, 2, 0, 0.0});
+    }
     if (h->prec != WEO_F64)
-        for (int ring : {4, 8, 16})
-            for (int threads : {128, 256}) cands.push_back({1, threads, 1, ring});
-    for (const Cand &c : cands) {
-        h->algo = c.algo;
-        if (c.algo == 1) {
-            h->fused_threads = c.threads;
-            h->fused_ring = c.ring;
-        } else {
-            h->cfg[h->prec].threads = c.threads;
-            h->cfg[h->prec].rhs_block = c.rb;
-        }
+        for (int la : {4, 8})
+            for (int threads : {128, 256}) cands.push_back({1, threads, 1, 1, la, 0.0});
+    for (const TuneEntry &c : cands) {
+        apply_entry(h, c);
         bool ok = true;
         for (int w = 0; w < 2 && ok; ++w) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
         if (!ok) {
@@ -159,7 +160,10 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         ms /= reps;
-        if (ms < best.ms) best = {c.algo, c.threads, c.rb, c.ring, ms};
+        if (ms < best.ms) {
+            best = c;
+            best.ms = ms;
+        }
     }
     h->prof = saved_prof;
     cudaEventDestroy(e0);
@@ -168,17 +172,10 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     out.release();
     h->cfg[h->prec] = saved;
     h->algo = saved_algo;
-    h->fused_ring = saved_ring;
+    h->fused_lookahead = saved_la;
     h->fused_threads = saved_fthreads;
     if (best.ms >= 1e30) return set_error(WEO_ERR_CUDA, "no launch configuration ran");
-    h->algo = best.algo;
-    if (best.algo == 1) {
-        h->fused_threads = best.threads;
-        h->fused_ring = best.ring;
-    } else {
-        h->cfg[h->prec].threads = best.threads;
-        h->cfg[h->prec].rhs_block = best.rhs_block;
-    }
+    apply_entry(h, best);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;
@@ -218,11 +215,11 @@ extern "C" int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block)
     return WEO_OK;
 }
 
-extern "C" int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *ring, int *threads)
+extern "C" int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *lookahead, int *threads)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
     if (algo) *algo = h->algo;
-    if (ring) *ring = h->fused_ring;
+    if (lookahead) *lookahead = h->fused_lookahead;
     if (threads) *threads = h->fused_threads;
     return WEO_OK;
 }

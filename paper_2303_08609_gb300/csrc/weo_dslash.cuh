@@ -207,4 +207,18 @@ __global__ void __launch_bounds__(256, 4) hop_kernel_occ(const HopParams p)
     hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, blockIdx.y * R);
 }
 
+// Right-hand sides on neighbouring lanes: NL consecutive threads take one site
+// and NL different right-hand sides. Their link loads read the same addresses,
+// so each warp fetches a link once for NL right-hand sides, while every thread
+// keeps the register footprint of a single right-hand side.
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NL>
+__global__ void __launch_bounds__(256, 4) hop_kernel_lanes(const HopParams p)
+{
+    const int b = p.reverse ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int i = b * (int)(blockDim.x / NL) + (int)threadIdx.x / NL;
+    const int r = (int)blockIdx.y * NL + (int)threadIdx.x % NL;
+    if (i >= p.vh || r >= p.nrhs) return;
+    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, 1>(p, i, r);
+}
+
 }  // namespace weo

@@ -65,7 +65,8 @@ struct PackedGauge {
 // Launch configuration chosen by the tuner (or defaults).
 struct LaunchCfg {
     int threads = 128;
-    int rhs_block = 1;
+    int rhs_block = 1;   // right-hand sides per thread (register blocking)
+    int lanes = 1;       // right-hand sides on neighbouring lanes sharing link loads
 };
 
 struct Profiler;
@@ -95,9 +96,8 @@ struct wilson_eo_s {
     // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
     int algo = 0;
     int alternate = 1;       // second hop walks the sites in reverse order
-    int fused_ring = 8;
+    int fused_lookahead = 8;     // t-slices the fused kernel's first hop runs ahead
     int fused_threads = 128;
-    weo::Buffer fused_tmp;   // ring of odd-site t-slices
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
     weo::Buffer halo;        // face buffers of the domain-decomposed hop
 };
@@ -137,8 +137,9 @@ int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, c
 // spinor formats) and odd-site buffer (api.cu)
 int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const void *in,
              int nrhs, bool dag, cudaStream_t s);
-// fused.cu: single-launch M_eo with FP32 spinors; error word of bounded waits
-int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *out, const void *in, bool dag,
+// fused.cu: both hops in one persistent launch over a wavefront of t-slices
+// (FP32 spinors, odd intermediate in `mid`); error word of its bounded waits
+int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, const void *in, bool dag,
               cudaStream_t s, bool inject_timeout = false);
 int fused_take_error(wilson_eo_s *h, cudaStream_t s, unsigned int *err);
 int fused_prepare(wilson_eo_s *h, cudaStream_t s);

@@ -8,9 +8,28 @@
 
 namespace weo {
 
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NL>
+int launch_lanes(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
+{
+    const int sites = cfg.threads / NL;
+    dim3 grid((unsigned)((p.vh + sites - 1) / sites), (unsigned)((p.nrhs + NL - 1) / NL));
+    hop_kernel_lanes<SIn, SOut, SX, Lk, Dag, Axpy, NL><<<grid, cfg.threads, 0, s>>>(p);
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
+    if constexpr (R == 1 && sizeof(typename SOut::real) == 4) {
+        // right-hand sides sharing link loads across lanes (never more lanes than
+        // right-hand sides)
+        int nl = cfg.lanes;
+        while (nl > 1 && nl > p.nrhs) nl /= 2;
+        if (nl == 8) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 8>(p, cfg, s);
+        if (nl == 4) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 4>(p, cfg, s);
+        if (nl == 2) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 2>(p, cfg, s);
+    }
     const int threads = cfg.threads;
     dim3 grid((unsigned)((p.vh + threads - 1) / threads), (unsigned)((p.nrhs + R - 1) / R));
     // the 64-register cap pays for 18-real FP32 and 16-bit links; the FP32

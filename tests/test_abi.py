@@ -107,3 +107,7 @@ def test_alu_peak_rejects_other_precisions(lib):
     with pytest.raises(weo.WilsonEOError) as e:
         weo.wilson_eo_alu_peak("f16")
     assert e.value.status == -1
+
+
+def test_rhs_lanes_rejects_bad_values(lib):
+    assert lib.wilson_eo_set_rhs_lanes(None, 2) == -1

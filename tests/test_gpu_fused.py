@@ -1,7 +1,8 @@
-"""The fused single-launch M_eo (wavefront over t-slices, odd intermediate in an
-L2 ring) against the oracle and against the two-launch path, for every link
-format it supports, ring sizes from the minimum (3) up, both CTA sizes, and
-lattices whose t extent is smaller than, equal to and larger than the ring."""
+"""The fused single-launch M_eo (both hops in one persistent launch, the first
+hop running `lookahead` t-slices ahead of the second) against the oracle and,
+bit for bit, against the two-launch path (same per-site code), for every link
+format, lookaheads from 1 to beyond Lt (clamped to Lt - 1), both CTA sizes, and
+t extents from 2 up."""
 
 import numpy as np
 import pytest
@@ -22,8 +23,8 @@ def weo():
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 2), (4, 4, 4, 4), (8, 4, 6, 6), (8, 8, 8, 8),
                                   (4, 6, 2, 22), (6, 4, 4, 40)])
-@pytest.mark.parametrize("ring,threads", [(3, 128), (8, 256), (16, 128)])
-def test_fused_matches_oracle(weo, oracle_lib, dims, ring, threads):
+@pytest.mark.parametrize("lookahead,threads", [(1, 128), (2, 256), (8, 128), (64, 256)])
+def test_fused_matches_oracle(weo, oracle_lib, dims, lookahead, threads):
     import torch
 
     U = gen.gauge_field(dims, "haar", seed=100)
@@ -31,31 +32,35 @@ def test_fused_matches_oracle(weo, oracle_lib, dims, ring, threads):
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
     x = to_device(to_planar(psi), "f32")
     ref = {d: op.apply(x, dag=d) for d in (False, True)}
-    weo.wilson_eo_set_algorithm(op.handle, "fused", ring, threads)
+    weo.wilson_eo_set_algorithm(op.handle, "fused", lookahead, threads)
     for dag in (False, True):
         y = op.apply(x, dag=dag)
         weo.wilson_eo_check(op.handle)
         f = oracle_lib.meo_dag if dag else oracle_lib.meo
         assert rel_l2(from_planar(y.cpu().numpy()), f(U, 0.13, psi, dims)) <= TOL["f32"]
-        assert rel_l2(y.cpu().numpy(), ref[dag].cpu().numpy()) <= 1e-6
+        assert torch.equal(y, ref[dag])
     op.close()
 
 
 @pytest.mark.parametrize("prec,fmt", [("f32", 12), ("f16", 18), ("f16", 12), ("bf16", 18),
                                       ("bf16", 12)])
 def test_fused_link_formats(weo, oracle_lib, prec, fmt):
+    import torch
+
     dims = (8, 8, 8, 16)
     U = gen.gauge_field(dims, "smooth", seed=102, eps=0.4)
     psi = gen.gaussian_spinor(dims, nrhs=2, seed=103)
     op = weo.WilsonEO(dims, 0.125, to_device(U), prec=prec, linkfmt=fmt)
-    weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
     x = to_device(to_planar(psi), "f32")
+    ref = {d: op.apply(x, dag=d) for d in (False, True)}
+    weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
     for dag in (False, True):
         y = op.apply(x, dag=dag)
         weo.wilson_eo_check(op.handle)
         f = oracle_lib.meo_dag if dag else oracle_lib.meo
         for r in range(2):
             assert rel_l2(from_planar(y[r].cpu().numpy()), f(U, 0.125, psi[r], dims)) <= TOL[prec]
+        assert torch.equal(y, ref[dag])
     op.close()
 
 
@@ -81,7 +86,7 @@ def test_fused_full_size_sampled_and_solver(weo, oracle_lib):
     Us = gen.gauge_field(small, "smooth", seed=104, eps=0.4)
     b = gen.gaussian_spinor(small, seed=105)[0]
     op = weo.WilsonEO(small, 0.13, to_device(Us), prec="f16")
-    weo.wilson_eo_set_algorithm(op.handle, "fused", 3, 128)
+    weo.wilson_eo_set_algorithm(op.handle, "fused", 1, 128)
     xs, info = op.solve(to_device(to_planar(b)), tol=1e-10, mixed=True)
     weo.wilson_eo_check(op.handle)
     assert info["converged"]
