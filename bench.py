@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--linkfmt", type=int, default=18)
     ap.add_argument("--algo", type=int, default=0, help="0: two hop launches, 1: fused")
-    ap.add_argument("--lookahead", type=int, default=8,
+    ap.add_argument("--lookahead", type=int, default=4,
                     help="t-slices the fused kernel's first hop runs ahead of the second")
     ap.add_argument("--threads", type=int, default=128, help="threads per CTA of the hop kernels")
     ap.add_argument("--order", type=int, default=1,
@@ -90,6 +90,11 @@ def fields(seed=0):
 
 # sources that define the FP32 hopping kernels whose DRAM traffic ncu measured
 HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "weo_launch.cuh", "dslash_f32.cu")
+
+
+def sources_for(label):
+    """Source files a kernel label's code comes from."""
+    return HOP_SOURCES + ("fused.cu",) if label.startswith("fused_") else HOP_SOURCES
 
 
 def kernel_source_hash(files=HOP_SOURCES):
@@ -174,7 +179,7 @@ def stored_traffic(label):
         return None
     d = json.load(open(p))
     e = d.get(label)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(sources_for(label)):
         return None
     return e.get("bytes_per_launch")
 
@@ -629,7 +634,7 @@ def solve_comparison(dev, dims, only=None):
     bd = torch.from_numpy(np.ascontiguousarray(np.moveaxis(b, 0, -1))).to(dev)
     del b
     res = {"lattice": list(dims), "kappa": 0.135, "tol": 1e-10, "field_gen_s": round(gen_s, 1),
-           "note": "fused: inner M_eo in one persistent launch (first hop 8 t-slices ahead); "
+           "note": "fused: inner M_eo in one persistent launch (first hop 4 t-slices ahead); "
                    "two_pass: two hop launches; both keep the odd intermediate in 16-bit "
                    "for 16-bit handles and give identical iterates"}
     for name, prec, mixed, algo in (("mixed_f16_fused", "f16", True, 1),
@@ -642,7 +647,7 @@ def solve_comparison(dev, dims, only=None):
             continue
         op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=18)
         if algo:
-            weo.wilson_eo_set_algorithm(op.handle, "fused", 8, 128)
+            weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
         if "delta" in name:
             weo.wilson_eo_solver_config(op.handle, delta=float(name.split("delta")[1]))
         try:

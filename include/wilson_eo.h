@@ -252,7 +252,7 @@ int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out
  *   algo 1  one persistent launch for both hops of Eq. 4: CTAs take (hop,
  *           t-slice, chunk) items from a queue in which the first hop H_oe
  *           runs `lookahead` t-slices ahead of the second (1..64, clamped to
- *           Lt-1; 0 keeps the current value, default 8), so the second hop
+ *           Lt-1; 0 keeps the current value, default 4), so the second hop
  *           finds the links and the odd-site intermediate of its slices still
  *           in L2; `threads` per CTA 128 or 256 (0 keeps the current value).
  *           Same arithmetic and intermediate format as algo 0, so the

@@ -126,7 +126,7 @@ __device__ __forceinline__ void fused_task(int L, int D, int k, bool &phase_b, i
     }
 }
 
-template <class SMid, class SMidL2, class Lk, bool Dag, int THREADS, int MINB>
+template <class SMid, class SMidL2, class LkA, class LkB, bool Dag, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) fused_meo_kernel(const FusedParams f)
 {
     __shared__ int sh_item;
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(THREADS, MINB) fused_meo_kernel(const FusedPar
         const int s = c * THREADS + (int)threadIdx.x;
         if (s < f.vs) {
             const int i = t * f.vs + s;
-            if (pb) hop_site<SMidL2, SpF32, SpF32, Lk, Dag, true, 1>(f.b, i, 0);
-            else hop_site<SpF32, SMid, SpF32, Lk, Dag, false, 1>(f.a, i, 0);
+            if (pb) hop_site<SMidL2, SpF32, SpF32, LkB, Dag, true, 1>(f.b, i, 0);
+            else hop_site<SpF32, SMid, SpF32, LkA, Dag, false, 1>(f.a, i, 0);
         }
         __syncthreads();
         if (threadIdx.x == 0 && !pb && !f.inject) {
@@ -166,11 +166,11 @@ __global__ void __launch_bounds__(THREADS, MINB) fused_meo_kernel(const FusedPar
     }
 }
 
-template <class SMid, class SMidL2, class Lk, bool Dag, int THREADS, int MINB>
+template <class SMid, class SMidL2, class LkA, class LkB, bool Dag, int THREADS, int MINB>
 static int launch_fused_v(FusedParams f, int sms, cudaStream_t s)
 {
     int per_sm = 0;
-    auto kern = fused_meo_kernel<SMid, SMidL2, Lk, Dag, THREADS, MINB>;
+    auto kern = fused_meo_kernel<SMid, SMidL2, LkA, LkB, Dag, THREADS, MINB>;
     f.chunks = (f.vs + THREADS - 1) / THREADS;
     f.total = 2 * f.lt * f.chunks;
     WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0));
@@ -183,22 +183,31 @@ static int launch_fused_v(FusedParams f, int sms, cudaStream_t s)
 // 128 threads with six CTAs per SM (85 registers) or 256 threads with three:
 // both measured faster than the 64-register cap of the two-launch kernels,
 // which makes this kernel (both hops' code in one body) spill heavily.
-template <class SMid, class SMidL2, class Lk, bool Dag>
+template <class SMid, class SMidL2, class LkA, class LkB, bool Dag>
 static int launch_fused_t(FusedParams f, int threads, cudaStream_t s)
 {
     int dev = 0, sms = 0;
     WEO_CUDA(cudaGetDevice(&dev));
     WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (threads == 256) return launch_fused_v<SMid, SMidL2, Lk, Dag, 256, 3>(f, sms, s);
-    return launch_fused_v<SMid, SMidL2, Lk, Dag, 128, 6>(f, sms, s);
+    if (threads == 256) return launch_fused_v<SMid, SMidL2, LkA, LkB, Dag, 256, 3>(f, sms, s);
+    return launch_fused_v<SMid, SMidL2, LkA, LkB, Dag, 128, 6>(f, sms, s);
 }
 
-template <class SMid, class SMidL2, class Lk>
+// The first hop reads the links with L2 retention (the second hop of the same
+// slice reads them again a few slices later), the second with evict-first.
+template <class SMid, class SMidL2, template <class> class LkOf>
 static int launch_fused_d(const FusedParams &f, bool dag, int threads, cudaStream_t s)
 {
-    return dag ? launch_fused_t<SMid, SMidL2, Lk, true>(f, threads, s)
-               : launch_fused_t<SMid, SMidL2, Lk, false>(f, threads, s);
+    using LkA = LkOf<LdL2>;
+    using LkB = LkOf<LdStream>;
+    return dag ? launch_fused_t<SMid, SMidL2, LkA, LkB, true>(f, threads, s)
+               : launch_fused_t<SMid, SMidL2, LkA, LkB, false>(f, threads, s);
 }
+
+template <class Ld> using LkH16_18_ = Lk16_18<H16Traits, Ld>;
+template <class Ld> using LkH16_12_ = Lk16_12<H16Traits, Ld>;
+template <class Ld> using LkB16_18_ = Lk16_18<B16Traits, Ld>;
+template <class Ld> using LkB16_12_ = Lk16_12<B16Traits, Ld>;
 
 // M_eo (or M_eo^dag) of one right-hand side with FP32 spinors through the
 // fused kernel, links from `g` (FP32 with an FP32 intermediate, or FP16 /
@@ -254,16 +263,16 @@ int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, const 
     int st;
     switch (g.prec) {
     case WEO_F32:
-        st = c ? launch_fused_d<SpF32, SpF32L2, LkF32_12>(f, dag, threads, s)
-               : launch_fused_d<SpF32, SpF32L2, LkF32_18>(f, dag, threads, s);
+        st = c ? launch_fused_d<SpF32, SpF32L2, LkF32_12T>(f, dag, threads, s)
+               : launch_fused_d<SpF32, SpF32L2, LkF32_18T>(f, dag, threads, s);
         break;
     case WEO_F16:
-        st = c ? launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_12>(f, dag, threads, s)
-               : launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_18>(f, dag, threads, s);
+        st = c ? launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_12_>(f, dag, threads, s)
+               : launch_fused_d<SpH16, Sp16L2<H16Traits>, LkH16_18_>(f, dag, threads, s);
         break;
     default:
-        st = c ? launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_12>(f, dag, threads, s)
-               : launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_18>(f, dag, threads, s);
+        st = c ? launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_12_>(f, dag, threads, s)
+               : launch_fused_d<SpB16, Sp16L2<B16Traits>, LkB16_18_>(f, dag, threads, s);
         break;
     }
     prof_end(h, tok, s);

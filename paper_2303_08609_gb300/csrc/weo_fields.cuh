@@ -76,7 +76,18 @@ __device__ __forceinline__ T ld_keep(const T *p) { return __ldg(p); }
 template <typename T>
 __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
 
-__device__ __forceinline__ uint2 ld_stream_u2(const uint2 *p) { return __ldcs(p); }
+
+// Load policies of the link fields. LdStream: the links are read once per pass
+// (evict first). LdL2: another CTA reads the same links again shortly (the
+// second hop of the fused M_eo): keep them in L2 at normal priority and skip L1.
+struct LdStream {
+    template <typename T>
+    __device__ static __forceinline__ T ld(const T *p) { return __ldcs(p); }
+};
+struct LdL2 {
+    template <typename T>
+    __device__ static __forceinline__ T ld(const T *p) { return __ldcg(p); }
+};
 
 // ---------------------------------------------------------------- spinors --
 
@@ -259,16 +270,17 @@ struct LkF64_12 {
     }
 };
 
-struct LkF32_18 {
+template <class Ld = LdStream>
+struct LkF32_18T {
     static constexpr int kBytesPerSite = 72;
     template <typename R>
     __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
                                                 cx<R> U[3][3])
     {
         const float4 *p = static_cast<const float4 *>(base);
-        float4 a = ld_stream(p + i), b = ld_stream(p + vh + i), c = ld_stream(p + 2 * vh + i),
-               d = ld_stream(p + 3 * vh + i);
-        float2 e = ld_stream(reinterpret_cast<const float2 *>(p + 4 * vh) + i);
+        float4 a = Ld::ld(p + i), b = Ld::ld(p + vh + i), c = Ld::ld(p + 2 * vh + i),
+               d = Ld::ld(p + 3 * vh + i);
+        float2 e = Ld::ld(reinterpret_cast<const float2 *>(p + 4 * vh) + i);
         U[0][0] = {R(a.x), R(a.y)};
         U[0][1] = {R(a.z), R(a.w)};
         U[0][2] = {R(b.x), R(b.y)};
@@ -291,14 +303,15 @@ struct LkF32_18 {
     }
 };
 
-struct LkF32_12 {
+template <class Ld = LdStream>
+struct LkF32_12T {
     static constexpr int kBytesPerSite = 48;
     template <typename R>
     __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
                                                 cx<R> U[3][3])
     {
         const float4 *p = static_cast<const float4 *>(base);
-        float4 a = ld_stream(p + i), b = ld_stream(p + vh + i), c = ld_stream(p + 2 * vh + i);
+        float4 a = Ld::ld(p + i), b = Ld::ld(p + vh + i), c = Ld::ld(p + 2 * vh + i);
         U[0][0] = {R(a.x), R(a.y)};
         U[0][1] = {R(a.z), R(a.w)};
         U[0][2] = {R(b.x), R(b.y)};
@@ -317,7 +330,7 @@ struct LkF32_12 {
     }
 };
 
-template <class Tr>
+template <class Tr, class Ld = LdStream>
 struct Lk16_18 {
     static constexpr int kBytesPerSite = 36;
     template <typename R>
@@ -325,8 +338,8 @@ struct Lk16_18 {
                                                 cx<R> U[3][3])
     {
         const uint4 *p = static_cast<const uint4 *>(base);
-        uint4 a = ld_stream(p + i), b = ld_stream(p + vh + i);
-        uint32_t e = ld_stream(reinterpret_cast<const unsigned int *>(p + 2 * vh) + i);
+        uint4 a = Ld::ld(p + i), b = Ld::ld(p + vh + i);
+        uint32_t e = Ld::ld(reinterpret_cast<const unsigned int *>(p + 2 * vh) + i);
         const uint32_t w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, e};
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -347,7 +360,7 @@ struct Lk16_18 {
     }
 };
 
-template <class Tr>
+template <class Tr, class Ld = LdStream>
 struct Lk16_12 {
     static constexpr int kBytesPerSite = 24;
     template <typename R>
@@ -355,8 +368,8 @@ struct Lk16_12 {
                                                 cx<R> U[3][3])
     {
         const uint4 *p = static_cast<const uint4 *>(base);
-        uint4 a = ld_stream(p + i);
-        uint2 b = ld_stream_u2(reinterpret_cast<const uint2 *>(p + vh) + i);
+        uint4 a = Ld::ld(p + i);
+        uint2 b = Ld::ld(reinterpret_cast<const uint2 *>(p + vh) + i);
         const uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -377,6 +390,8 @@ struct Lk16_12 {
     }
 };
 
+using LkF32_18 = LkF32_18T<>;
+using LkF32_12 = LkF32_12T<>;
 using LkH16_18 = Lk16_18<H16Traits>;
 using LkH16_12 = Lk16_12<H16Traits>;
 using LkB16_18 = Lk16_18<B16Traits>;

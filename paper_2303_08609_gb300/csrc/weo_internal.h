@@ -96,7 +96,7 @@ struct wilson_eo_s {
     // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
     int algo = 0;
     int alternate = 1;       // second hop walks the sites in reverse order
-    int fused_lookahead = 8;     // t-slices the fused kernel's first hop runs ahead
+    int fused_lookahead = 4;     // t-slices the fused kernel's first hop runs ahead
     int fused_threads = 128;
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
     weo::Buffer halo;        // face buffers of the domain-decomposed hop
