@@ -199,56 +199,49 @@ __device__ __forceinline__ void axpy4(float4 &y, float a, float4 x)
     y.w += a * x.w;
 }
 
-// x += alpha p ; r -= alpha Ap ; rr_new = |r|^2 ; beta = rr_new / rr ; rr = rr_new
+// r -= alpha Ap ; rr_new = |r|^2 ; beta = rr_new / rr ; rr = rr_new
+// (x += alpha p is done by k_cg_dir, which reads p anyway)
 template <typename T2>
-__global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T2 *p, const T2 *Ap,
-                                                           long long n, SolveScalars *scs)
+__global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *r, const T2 *Ap, long long n,
+                                                           SolveScalars *scs)
 {
     SolveScalars *sc = scs + blockIdx.y;
     if (!sc->active || sc->nonfinite) return;
     using T = decltype(T2().x);
     const long long o = blockIdx.y * n;
-    x += o;
     r += o;
-    p += o;
     Ap += o;
     const T alpha = T(sc->alpha);
     double v = 0.0;
     if constexpr (std::is_same<T2, float2>::value) {
-        float4 *x4 = reinterpret_cast<float4 *>(x), *r4 = reinterpret_cast<float4 *>(r);
-        const float4 *p4 = reinterpret_cast<const float4 *>(p), *a4 = reinterpret_cast<const float4 *>(Ap);
+        float4 *r4 = reinterpret_cast<float4 *>(r);
+        const float4 *a4 = reinterpret_cast<const float4 *>(Ap);
         const long long n4 = n >> 1, st = grid_stride();
         long long k = grid_index();
-        for (; k + st < n4; k += 2 * st) {
-            float4 x0 = x4[k], x1 = x4[k + st], r0 = r4[k], r1 = r4[k + st];
-            const float4 p0 = p4[k], p1 = p4[k + st], a0 = a4[k], a1 = a4[k + st];
-            axpy4(x0, alpha, p0);
-            axpy4(x1, alpha, p1);
-            axpy4(r0, -alpha, a0);
-            axpy4(r1, -alpha, a1);
-            x4[k] = x0;
-            x4[k + st] = x1;
+        for (; k + 3 * st < n4; k += 4 * st) {
+            float4 r0 = r4[k], r1 = r4[k + st], r2 = r4[k + 2 * st], r3 = r4[k + 3 * st];
+            axpy4(r0, -alpha, a4[k]);
+            axpy4(r1, -alpha, a4[k + st]);
+            axpy4(r2, -alpha, a4[k + 2 * st]);
+            axpy4(r3, -alpha, a4[k + 3 * st]);
             r4[k] = r0;
             r4[k + st] = r1;
-            v += double(sq4(r0) + sq4(r1));
+            r4[k + 2 * st] = r2;
+            r4[k + 3 * st] = r3;
+            v += double((sq4(r0) + sq4(r1)) + (sq4(r2) + sq4(r3)));
         }
-        if (k < n4) {
-            float4 x0 = x4[k], r0 = r4[k];
-            axpy4(x0, alpha, p4[k]);
+        for (; k < n4; k += st) {
+            float4 r0 = r4[k];
             axpy4(r0, -alpha, a4[k]);
-            x4[k] = x0;
             r4[k] = r0;
             v += double(sq4(r0));
         }
     } else {
         FOR_ELEMENTS(k) {
-            T2 xv = x[k], rv = r[k];
-            const T2 pv = p[k], av = Ap[k];
-            xv.x += alpha * pv.x;
-            xv.y += alpha * pv.y;
+            T2 rv = r[k];
+            const T2 av = Ap[k];
             rv.x -= alpha * av.x;
             rv.y -= alpha * av.y;
-            x[k] = xv;
             r[k] = rv;
             v += re_dot(rv, rv);
         }
@@ -265,42 +258,55 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_update(T2 *x, T2 *r, const T
     }
 }
 
-// p = r + beta p
+// x += alpha p ; p = r + beta p
 template <typename T2>
-__global__ void __launch_bounds__(kRedThreads) k_cg_dir(T2 *p, const T2 *r, long long n, const SolveScalars *scs)
+__global__ void __launch_bounds__(kRedThreads) k_cg_dir(T2 *x, T2 *p, const T2 *r, long long n,
+                                                        const SolveScalars *scs)
 {
     const SolveScalars *sc = scs + blockIdx.y;
     if (!sc->active || sc->nonfinite) return;
     using T = decltype(T2().x);
     const long long o = blockIdx.y * n;
+    x += o;
     p += o;
     r += o;
-    const T beta = T(sc->beta);
+    const T alpha = T(sc->alpha), beta = T(sc->beta);
     if constexpr (std::is_same<T2, float2>::value) {
-        float4 *p4 = reinterpret_cast<float4 *>(p);
+        float4 *x4 = reinterpret_cast<float4 *>(x), *p4 = reinterpret_cast<float4 *>(p);
         const float4 *r4 = reinterpret_cast<const float4 *>(r);
         const long long n4 = n >> 1, st = grid_stride();
         long long k = grid_index();
         for (; k + st < n4; k += 2 * st) {
             const float4 q0 = p4[k], q1 = p4[k + st];
-            float4 y0 = r4[k], y1 = r4[k + st];
+            float4 x0 = x4[k], x1 = x4[k + st], y0 = r4[k], y1 = r4[k + st];
+            axpy4(x0, alpha, q0);
+            axpy4(x1, alpha, q1);
             axpy4(y0, beta, q0);
             axpy4(y1, beta, q1);
+            x4[k] = x0;
+            x4[k + st] = x1;
             p4[k] = y0;
             p4[k + st] = y1;
         }
         if (k < n4) {
-            float4 y0 = r4[k];
-            axpy4(y0, beta, p4[k]);
+            const float4 q0 = p4[k];
+            float4 x0 = x4[k], y0 = r4[k];
+            axpy4(x0, alpha, q0);
+            axpy4(y0, beta, q0);
+            x4[k] = x0;
             p4[k] = y0;
         }
     } else {
         FOR_ELEMENTS(k) {
-            T2 pv = p[k];
-            const T2 rv = r[k];
-            pv.x = rv.x + beta * pv.x;
-            pv.y = rv.y + beta * pv.y;
-            p[k] = pv;
+            const T2 pv = p[k], rv = r[k];
+            T2 xv = x[k];
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            x[k] = xv;
+            T2 q;
+            q.x = rv.x + beta * pv.x;
+            q.y = rv.y + beta * pv.y;
+            p[k] = q;
         }
     }
 }
@@ -472,15 +478,15 @@ static int cg_iteration(wilson_eo_s *h, SolverState *S, const PackedGauge &g, bo
     if (mixed) {
         WEO_TRY(normal_op(h, S, g, S->oddlo, S->t32.ptr, S->Ap.ptr, S->p.ptr, s));
         k_norm2<float2><<<grid, kRedThreads, 0, s>>>((const float2 *)S->t32.ptr, n, sc, 2);
-        k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->rs.ptr,
-                                                          (const float2 *)S->p.ptr, (const float2 *)S->Ap.ptr, n, sc);
-        k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->p.ptr, (const float2 *)S->rs.ptr, n, sc);
+        k_cg_update<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->rs.ptr, (const float2 *)S->Ap.ptr, n, sc);
+        k_cg_dir<float2><<<grid, kRedThreads, 0, s>>>((float2 *)S->xs.ptr, (float2 *)S->p.ptr,
+                                                       (const float2 *)S->rs.ptr, n, sc);
     } else {
         WEO_TRY(normal_op(h, S, g, S->odd64, S->e64.ptr, S->Ap64.ptr, S->p64.ptr, s));
         k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->e64.ptr, n, sc, 2);
-        k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->r64.ptr,
-                                                           (const double2 *)S->p64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
-        k_cg_dir<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->p64.ptr, (const double2 *)S->r64.ptr, n, sc);
+        k_cg_update<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->r64.ptr, (const double2 *)S->Ap64.ptr, n, sc);
+        k_cg_dir<double2><<<grid, kRedThreads, 0, s>>>((double2 *)S->x64.ptr, (double2 *)S->p64.ptr,
+                                                        (const double2 *)S->r64.ptr, n, sc);
     }
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
