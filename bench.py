@@ -431,6 +431,34 @@ def run_ours(args, rank, world, local):
             variants[f"{prec}_l{fmt}" + ("_fused" if algo else "")] = ent
             o2.close()
             del xv, yv, zv
+        # float-float M_eo (FP64-class accuracy on the FP32 pipes) on complex128 spinors
+        o2 = weo.WilsonEO(DIMS, KAPPA, Ud, prec="f64")
+        xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev)
+        yv, zv = torch.empty_like(xv), torch.empty_like(xv)
+        for _ in range(3):
+            weo.wilson_eo_apply_ff64(o2.handle, yv, xv, 1, False, stream)
+            weo.wilson_eo_apply_ff64(o2.handle, zv, yv, 1, True, stream)
+        torch.cuda.synchronize()
+        n = 20
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n):
+            weo.wilson_eo_apply_ff64(o2.handle, yv, xv, 1, False, stream)
+            weo.wilson_eo_apply_ff64(o2.handle, zv, yv, 1, True, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        vms = a0.elapsed_time(a1) / n
+        ent = {"gflops": round(flops_step / (vms * 1e-3) / 1e9, 1), "ms_per_step": round(vms, 4),
+               "note": "float-float arithmetic (hi + lo floats, ~48 bits), complex128 in and out"}
+        if rank == 0 and check and "error" not in check:
+            yo = np.moveaxis(yv[:, :, torch.from_numpy(sites).to(dev)].cpu().numpy(), -1, 0)
+            ent["meo_rel_l2_64_sites"] = float(np.linalg.norm(yo - want_y) / np.linalg.norm(want_y))
+        if variants.get("f64_l18"):
+            ent["speedup_vs_native_f64"] = round(ent["gflops"] / variants["f64_l18"]["gflops"], 2)
+        variants["ff64_l18"] = ent
+        o2.close()
+        del xv, yv, zv
         del Ud
 
     extra = {} if args.no_extras else extras(U, psi, dev, stream)
@@ -636,11 +664,14 @@ def solve_comparison(dev, dims, only=None):
     res = {"lattice": list(dims), "kappa": 0.135, "tol": 1e-10, "field_gen_s": round(gen_s, 1),
            "note": "fused: inner M_eo in one persistent launch (first hop 4 t-slices ahead); "
                    "two_pass: two hop launches; both keep the odd intermediate in 16-bit "
-                   "for 16-bit handles and give identical iterates"}
+                   "for 16-bit handles and give identical iterates; reliable-update residuals "
+                   "in float-float with an FP64 check before convergence, fp64res: native FP64 "
+                   "residuals"}
     for name, prec, mixed, algo in (("mixed_f16_fused", "f16", True, 1),
                                     ("mixed_bf16_fused", "bf16", True, 1),
                                     ("mixed_f32_fused", "f32", True, 1),
                                     ("mixed_f16_two_pass", "f16", True, 0),
+                                    ("mixed_f16_two_pass_fp64res", "f16", True, 0),
                                     ("mixed_f16_two_pass_delta0.03", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0)):
         if only and name not in only:
@@ -650,6 +681,8 @@ def solve_comparison(dev, dims, only=None):
             weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
         if "delta" in name:
             weo.wilson_eo_solver_config(op.handle, delta=float(name.split("delta")[1]))
+        if name.endswith("fp64res"):
+            weo.wilson_eo_solver_residual(op.handle, 0)
         try:
             x, info = op.solve(bd, tol=1e-10, maxiter=20000, mixed=mixed)
             res[name] = {k: (round(v, 4) if isinstance(v, float) and k == "seconds" else v)

@@ -210,11 +210,22 @@ int wilson_eo_solve_multi(wilson_eo_t h, void *x_e, const void *b_e, int nrhs, d
  * leaves that setting unchanged. */
 int wilson_eo_solver_config(wilson_eo_t h, double delta, int chunk, int use_graphs);
 
+/* How the mixed-precision solver forms the true residual b - A x of a
+ * reliable update: mode 1 (default) with the float-float operator of
+ * wilson_eo_apply_ff64 (FP64-class accuracy, several times faster than native
+ * FP64 on GPUs with a reduced FP64 rate), and whenever that residual says a
+ * system has met tol, once more with the native FP64 operator, which alone
+ * decides convergence; mode 0 with the native FP64 operator every time. Plain
+ * FP64 solves always use the native FP64 operator. Other modes: WEO_ERR_ARG. */
+int wilson_eo_solver_residual(wilson_eo_t h, int mode);
+
 /* Statistics of the handle's last solve: low-precision (or FP64 in plain mode)
- * CG iterations, reliable updates, FP64 operator applications (true
- * residuals), wall seconds. Any pointer may be NULL. */
+ * CG iterations, reliable updates, native FP64 operator applications (true
+ * residuals), float-float operator applications (true residuals of reliable
+ * updates, see wilson_eo_solver_residual), wall seconds. Any pointer may be
+ * NULL. */
 int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
-                          int *fp64_applies, double *seconds);
+                          int *fp64_applies, int *ff_applies, double *seconds);
 
 /* M_eo (dag = 0) or M_eo^dag on n lattices at once, in ONE persistent
  * cooperative kernel launch: every lattice keeps its own extents, kappa and
@@ -313,6 +324,18 @@ int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order);
  * turns it off. WEO_ERR_ARG for other values, WEO_ERR_UNSUPPORTED for lanes > 1
  * on an FP64 handle. */
 int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes);
+
+/* M_eo in_e (dag = 0) or M_eo^dag in_e (dag = 1) in float-float arithmetic:
+ * every real is carried as an unevaluated sum hi + lo of two floats (about 48
+ * significant bits; error-free two-sum and FMA-based two-product), so the
+ * result has FP64-class accuracy (relative error ~1e-14) while all arithmetic
+ * runs on the FP32 pipes. Works on any handle, whatever its precision: the
+ * links come from the handle's canonical gauge field, split into float-float
+ * once (4V x 144 bytes, kept until set_gauge). in_e / out_e: nrhs canonical
+ * complex128 even spinors (host or device, as for wilson_eo_apply); the
+ * handle keeps three float-float work fields of the same size. Same errors
+ * as wilson_eo_apply. */
+int wilson_eo_apply_ff64(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, int dag, void *stream);
 
 /* Per-kernel timing. With profiling on, every kernel the handle launches is
  * bracketed by two CUDA events on its stream (a few microseconds of host time

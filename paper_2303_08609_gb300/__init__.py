@@ -83,7 +83,9 @@ def _load():
         "wilson_eo_prepare_source": (I, [P, P, P, P, P]),
         "wilson_eo_reconstruct": (I, [P, P, P, P, P]),
         "wilson_eo_solve_full": (I, [P, P, P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
-        "wilson_eo_solve_stats": (I, [P, IP, IP, IP, ctypes.POINTER(D)]),
+        "wilson_eo_solve_stats": (I, [P, IP, IP, IP, IP, ctypes.POINTER(D)]),
+        "wilson_eo_solver_residual": (I, [P, I]),
+        "wilson_eo_apply_ff64": (I, [P, P, P, I, I, P]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(P), I, P]),
         "wilson_eo_apply_batch_rhs": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -384,12 +386,25 @@ def wilson_eo_solver_config(h, delta=-1.0, chunk=0, use_graphs=-1):
 
 
 def wilson_eo_solve_stats(h):
-    it, ru, hi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    it, ru, hi, fa = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     sec = ctypes.c_double()
     _check(_load().wilson_eo_solve_stats(h, ctypes.byref(it), ctypes.byref(ru), ctypes.byref(hi),
-                                         ctypes.byref(sec)), "wilson_eo_solve_stats")
+                                         ctypes.byref(fa), ctypes.byref(sec)), "wilson_eo_solve_stats")
     return {"iterations": it.value, "reliable_updates": ru.value, "fp64_applies": hi.value,
-            "seconds": sec.value}
+            "ff_applies": fa.value, "seconds": sec.value}
+
+
+def wilson_eo_solver_residual(h, mode):
+    """True residuals of reliable updates: 1 float-float (FP64 confirms
+    convergence), 0 native FP64."""
+    _check(_load().wilson_eo_solver_residual(h, int(mode)), "wilson_eo_solver_residual")
+
+
+def wilson_eo_apply_ff64(h, out_e, in_e, nrhs=1, dag=False, stream=None):
+    """M_eo (or M_eo^dag) in float-float arithmetic on complex128 spinors."""
+    _expect(h, (out_e, in_e), nrhs, kind="spinor64", where="wilson_eo_apply_ff64")
+    _check(_load().wilson_eo_apply_ff64(h, _ptr(out_e), _ptr(in_e), int(nrhs), int(bool(dag)),
+                                        _stream(stream)), "wilson_eo_apply_ff64")
 
 
 def wilson_eo_apply_batch(handles, outs, ins, dag=False, stream=None):
@@ -546,6 +561,16 @@ class WilsonEO:
         nrhs = self._nrhs(psi)
         out = torch.empty_like(psi) if out is None else out
         (wilson_eo_apply_dag if dag else wilson_eo_apply)(self._h, out, psi, nrhs, stream)
+        return out
+
+    def apply_ff64(self, psi, dag=False, out=None, stream=None):
+        """M_eo psi (or M_eo^dag psi) in float-float arithmetic (FP64-class
+        accuracy on the FP32 pipes); psi and the result are complex128."""
+        import torch
+
+        nrhs = self._nrhs(psi)
+        out = torch.empty_like(psi) if out is None else out
+        wilson_eo_apply_ff64(self._h, out, psi, nrhs, dag, stream)
         return out
 
     def hop(self, psi, out_parity, dag=False, out=None, stream=None):

@@ -135,6 +135,7 @@ static int upload_gauge(wilson_eo_s *h, const void *gauge, int gauge_is_f64, cud
     h->canon_is_f64 = gauge_is_f64 ? 1 : 0;
     h->gauge_f64.valid = false;
     h->gauge_lo.valid = false;
+    h->gauge_ff.valid = false;
     WEO_TRY(pack_gauge(h, h->gauge, h->prec, h->fmt, h->canon_gauge.ptr, h->canon_is_f64, s));
     WEO_CUDA(cudaStreamSynchronize(s));
     return WEO_OK;
@@ -161,7 +162,7 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
              int nrhs, bool dag, cudaStream_t s)
 {
     const int prec = g.prec;
-    if (h->algo == 1 && prec != WEO_F64) {
+    if (h->algo == 1 && prec != WEO_F64 && prec != kPrecFF) {
         const long long ext32 = h->vh * 96;
         WEO_TRY(tmp.ensure((size_t)h->vh * (prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16))));
         for (int r = 0; r < nrhs; ++r)
@@ -173,8 +174,8 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
     p.nrhs = nrhs;
     p.gauge = static_cast<const char *>(g.buf.ptr);
     p.gauge_pb = g.pb;
-    const long long ext = h->vh * (prec == WEO_F64 ? 192 : 96);
-    if (prec == WEO_F64 || prec == WEO_F32) {
+    const long long ext = h->vh * (prec == WEO_F64 || prec == kPrecFF ? 192 : 96);
+    if (prec == WEO_F64 || prec == WEO_F32 || prec == kPrecFF) {
         WEO_TRY(tmp.ensure((size_t)ext * nrhs));
         p.out_parity = 1;
         p.in = in;
@@ -234,11 +235,44 @@ static int apply_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, 
     return finish_out(out_e, out, bytes, out_host, s);
 }
 
+static int apply_ff_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, bool dag,
+                           void *stream)
+{
+    if (!h || !out_e || !in_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+    if (nrhs < 1) return set_error(WEO_ERR_ARG, "nrhs must be >= 1");
+    if (out_e == in_e) return set_error(WEO_ERR_ARG, "out_e must not alias in_e");
+    DeviceGuard g(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)h->vh * 192 * (size_t)nrhs;  // complex128 and float-float alike
+    const void *in;
+    void *out;
+    bool out_host;
+    WEO_TRY(stage_in(h->stage_in, in_e, bytes, s, &in));
+    WEO_TRY(stage_out(h->stage_out, out_e, bytes, &out, &out_host));
+    const PackedGauge *gf = nullptr;
+    WEO_TRY(ff_gauge(h, &gf, s));
+    WEO_TRY(h->ff_in.ensure(bytes));
+    WEO_TRY(h->ff_out.ensure(bytes));
+    WEO_TRY(ff_from_f64(h->ff_in.ptr, in, h->vh, nrhs, s));
+    WEO_TRY(meo_with(h, *gf, h->ff_tmp, h->ff_out.ptr, h->ff_in.ptr, nrhs, dag, s));
+    WEO_TRY(ff_to_f64(out, h->ff_out.ptr, h->vh, nrhs, s));
+    return finish_out(out_e, out, bytes, out_host, s);
+}
+
 }  // namespace weo
 
 using namespace weo;
 
 extern "C" {
+
+int wilson_eo_apply_ff64(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, int dag, void *stream)
+{
+    try {
+        return apply_ff_common(h, out_e, in_e, nrhs, dag != 0, stream);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_apply_ff64");
+    }
+}
 
 int wilson_eo_create(wilson_eo_t *out, const int dims[4], double kappa, int prec, int linkfmt,
                      const void *gauge, int gauge_is_f64, void *stream)
@@ -394,6 +428,7 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
     if (kappa) *kappa = h->kappa;
     if (device_bytes)
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
+                        h->gauge_ff.buf.bytes + h->ff_in.bytes + h->ff_out.bytes + h->ff_tmp.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
                         h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes +
                         h->stage_in.bytes +
@@ -626,10 +661,21 @@ int wilson_eo_solver_config(wilson_eo_t h, double delta, int chunk, int use_grap
 }
 
 int wilson_eo_solve_stats(wilson_eo_t h, int *iterations, int *reliable_updates,
-                          int *fp64_applies, double *seconds)
+                          int *fp64_applies, int *ff_applies, double *seconds)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
-    return solver_stats(h, iterations, reliable_updates, fp64_applies, seconds);
+    return solver_stats(h, iterations, reliable_updates, fp64_applies, ff_applies, seconds);
+}
+
+int wilson_eo_solver_residual(wilson_eo_t h, int mode)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        DeviceGuard dg(h->device);
+        return solver_residual_mode(h, mode);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solver_residual");
+    }
 }
 
 void wilson_eo_destroy(wilson_eo_t h)
@@ -640,6 +686,10 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->gauge.buf.release();
     h->gauge_f64.buf.release();
     h->gauge_lo.buf.release();
+    h->gauge_ff.buf.release();
+    h->ff_in.release();
+    h->ff_out.release();
+    h->ff_tmp.release();
     h->canon_gauge.release();
     h->tmp.release();
     h->tmp2.release();

@@ -114,6 +114,7 @@ int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *ca
     case WEO_F32: st = c ? pack_with<LkF32_12>(g, h, canon, is_f64, s) : pack_with<LkF32_18>(g, h, canon, is_f64, s); break;
     case WEO_F16: st = c ? pack_with<LkH16_12>(g, h, canon, is_f64, s) : pack_with<LkH16_18>(g, h, canon, is_f64, s); break;
     case WEO_BF16: st = c ? pack_with<LkB16_12>(g, h, canon, is_f64, s) : pack_with<LkB16_18>(g, h, canon, is_f64, s); break;
+    case kPrecFF: st = pack_with<LkFF18>(g, h, canon, is_f64, s); break;
     default: return set_error(WEO_ERR_ARG, "unknown precision");
     }
     if (st == WEO_OK) g.valid = true;
@@ -129,6 +130,7 @@ int launch_hop(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &
     case WEO_F32: return launch_hop_f32(fmt, dag, axpy, p, cfg, s);
     case WEO_F16: return launch_hop_h16(fmt, io, dag, axpy, p, cfg, s);
     case WEO_BF16: return launch_hop_b16(fmt, io, dag, axpy, p, cfg, s);
+    case kPrecFF: return launch_hop_ff(dag, axpy, p, cfg, s);
     default: return set_error(WEO_ERR_ARG, "unknown precision");
     }
 }

@@ -99,10 +99,10 @@ void prof_end(wilson_eo_s *h, int token, cudaStream_t s)
 
 std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axpy)
 {
-    static const char *pn[] = {"f64", "f32", "f16", "bf16"};
+    static const char *pn[] = {"f64", "f32", "f16", "bf16", "ff"};
     std::string l = kind;
     l += "_";
-    l += (prec >= 0 && prec < 4) ? pn[prec] : "?";
+    l += (prec >= 0 && prec < 5) ? pn[prec] : "?";
     l += fmt == WEO_LINK12 ? "_l12" : "_l18";
     if (axpy) l += "_axpy";
     if (dag) l += "_dag";

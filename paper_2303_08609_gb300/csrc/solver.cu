@@ -65,6 +65,7 @@ struct SolverState {
     Buffer x64, b64, r64, e64, t64, odd64;     // FP64 work vectors
     Buffer xs, rs, p, Ap, t32, oddlo;          // low-precision work vectors
     Buffer p64, Ap64;                          // plain FP64 CG
+    Buffer xff, eff, tff, oddff;               // float-float true residuals
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [mixed]
     int graph_chunk[2] = {0, 0};
@@ -73,8 +74,9 @@ struct SolverState {
     int chunk = 8;
     int use_graphs = 1;
     int nrhs = 1;                    // right-hand sides of the current solve
+    int ff_residual = 1;             // mixed mode: reliable updates with the float-float operator
     // statistics of the last solve
-    int iterations = 0, reliable_updates = 0, hi_applies = 0;
+    int iterations = 0, reliable_updates = 0, hi_applies = 0, ff_applies = 0;
     double seconds = 0.0;
 };
 
@@ -332,6 +334,30 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(double2 *r, const doub
     if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) sc->red = tot;
 }
 
+// r = b - t with t in float-float (SpFF: 12 planes of high parts, then 12 of
+// low parts per right-hand side) ; red = |r|^2 (every right-hand side)
+__global__ void __launch_bounds__(kRedThreads) k_residual_ff(double2 *r, const double2 *b,
+                                                             const float2 *t, long long n,
+                                                             SolveScalars *scs)
+{
+    SolveScalars *sc = scs + blockIdx.y;
+    const long long o = blockIdx.y * n;
+    r += o;
+    b += o;
+    t += 2 * o;
+    double v = 0.0;
+    FOR_ELEMENTS(k) {
+        const float2 hi = t[k], lo = t[n + k];
+        const double2 bv = b[k];
+        const double2 rv = make_double2((bv.x - double(hi.x)) - double(lo.x), (bv.y - double(hi.y)) - double(lo.y));
+        r[k] = rv;
+        v += rv.x * rv.x + rv.y * rv.y;
+    }
+    v = block_sum(v);
+    double tot;
+    if (finish_reduction(sc, v, &tot) && threadIdx.x == 0) sc->red = tot;
+}
+
 // d = s over all right-hand sides (n_total elements)
 template <typename D2, typename S2>
 __global__ void k_convert(D2 *d, const S2 *s, long long n)
@@ -551,6 +577,42 @@ static int true_residual(wilson_eo_s *h, SolverState *S, const PackedGauge &ghi)
     return read_scalars(S);
 }
 
+// The same with the float-float operator (about 48 significant bits from FP32
+// arithmetic, several times the FP64 pipe's rate on GB300): x64 is split into
+// float-float, A x is formed in float-float, and r = b - A x in FP64.
+static int true_residual_ff(wilson_eo_s *h, SolverState *S)
+{
+    cudaStream_t s = S->stream;
+    const long long n = 12 * h->vh;
+    const size_t bytes = (size_t)h->vh * 192 * S->nrhs;
+    const PackedGauge *gff = nullptr;
+    WEO_TRY(ff_gauge(h, &gff, s));
+    WEO_TRY(S->xff.ensure(bytes));
+    WEO_TRY(S->eff.ensure(bytes));
+    WEO_TRY(S->tff.ensure(bytes));
+    WEO_TRY(ff_from_f64(S->xff.ptr, S->x64.ptr, h->vh, S->nrhs, s));
+    WEO_TRY(normal_op(h, S, *gff, S->oddff, S->eff.ptr, S->tff.ptr, S->xff.ptr, s));
+    k_residual_ff<<<dim3(red_grid(n), S->nrhs), kRedThreads, 0, s>>>(
+        (double2 *)S->r64.ptr, (const double2 *)S->b64.ptr, (const float2 *)S->tff.ptr, n, dev_scal(S));
+    WEO_CUDA(cudaGetLastError());
+    S->ff_applies += 1;
+    return read_scalars(S);
+}
+
+// True residual of a reliable update: float-float when enabled, and then, if
+// any active system looks converged, once more with the native FP64 operator,
+// so that convergence is only ever declared on an FP64 true residual.
+static int update_residual(wilson_eo_s *h, SolverState *S, const PackedGauge &ghi, bool ff,
+                           const std::vector<int> &active, const std::vector<double> &target)
+{
+    if (!ff) return true_residual(h, S, ghi);
+    WEO_TRY(true_residual_ff(h, S));
+    bool converged = false;
+    for (int r = 0; r < S->nrhs; ++r)
+        if (active[r] && S->host[r].red <= target[r]) converged = true;
+    return converged ? true_residual(h, S, ghi) : WEO_OK;
+}
+
 static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *iters_out,
                       double *relres_out)
 {
@@ -569,7 +631,8 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
     // reset every right-hand side's scalars and mark them active
     WEO_CUDA(cudaMemsetAsync(sc, 0, sizeof(SolveScalars) * R, s));
     for (int r = 0; r < R; ++r) WEO_TRY(set_flag(S, r, offsetof(SolveScalars, active), 1));
-    S->iterations = S->reliable_updates = S->hi_applies = 0;
+    S->iterations = S->reliable_updates = S->hi_applies = S->ff_applies = 0;
+    const bool ff = mixed && S->ff_residual;
     std::vector<int> active(R, 1), iters(R, 0);
     std::vector<double> target(R), rr_true(R), r_max(R), rr_min(R);
 
@@ -588,7 +651,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
     for (int r = 0; r < R; ++r)
         if (bb[r] == 0.0)
             WEO_CUDA(cudaMemsetAsync(static_cast<char *>(S->x64.ptr) + r * v64, 0, v64, s));
-    WEO_TRY(true_residual(h, S, *ghi));
+    WEO_TRY(update_residual(h, S, *ghi, ff, active, target));
     int n_active = R;
     auto retire = [&](int r) -> int {  // right-hand side r has converged
         active[r] = 0;
@@ -693,7 +756,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
             // recompute the residuals in FP64
             k_accumulate<<<flat_grid(nt), 256, 0, s>>>((double2 *)S->x64.ptr, (float2 *)S->xs.ptr, nt);
             WEO_CUDA(cudaGetLastError());
-            WEO_TRY(true_residual(h, S, *ghi));
+            WEO_TRY(update_residual(h, S, *ghi, ff, active, target));
             S->reliable_updates += 1;
             bool diverging = false;
             for (int r = 0; r < R; ++r) {
@@ -796,13 +859,23 @@ int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b
 }
 
 int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi_applies,
-                 double *seconds)
+                 int *ff_applies, double *seconds)
 {
     SolverState *S = h->solver;
     if (iterations) *iterations = S ? S->iterations : 0;
     if (reliable_updates) *reliable_updates = S ? S->reliable_updates : 0;
     if (hi_applies) *hi_applies = S ? S->hi_applies : 0;
+    if (ff_applies) *ff_applies = S ? S->ff_applies : 0;
     if (seconds) *seconds = S ? S->seconds : 0.0;
+    return WEO_OK;
+}
+
+int solver_residual_mode(wilson_eo_s *h, int mode)
+{
+    if (mode != 0 && mode != 1) return set_error(WEO_ERR_ARG, "mode must be 0 (FP64) or 1 (float-float)");
+    SolverState *S;
+    WEO_TRY(solver_state(h, &S));
+    S->ff_residual = mode;
     return WEO_OK;
 }
 

@@ -21,6 +21,8 @@
 // needs for its x and y shifts (Figs. 5-6).
 #pragma once
 
+#include <type_traits>
+
 #include "weo_fields.cuh"
 
 namespace weo {
@@ -103,15 +105,38 @@ __device__ __forceinline__ void hop_dir(cx<T> (&acc)[R][12], const HopParams &p,
 #pragma unroll
         for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
         cx<T> w[2][3];
+        if constexpr (std::is_same<T, ff>::value) {
+            // float-float: the six real products of each row are exact and
+            // independent; they are summed pairwise (short dependency chains)
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                cx<T> z = {T(0), T(0)};
+                for (int a = 0; a < 3; ++a) {
+                    ff re[6], im[6];
 #pragma unroll
-                for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[s][b], z) : cfmaconj(U[b][a], h[s][b], z);
-                w[s][a] = z;
-            }
+                    for (int b = 0; b < 3; ++b) {
+                        const cx<ff> u = FWD ? U[a][b] : U[b][a];
+                        const cx<ff> v = h[s][b];
+                        const ff ui = FWD ? u.i : -u.i;  // conj(u) for the backward hop
+                        re[2 * b] = ff_prod(u.r, v.r);
+                        re[2 * b + 1] = ff_prod(-ui, v.i);
+                        im[2 * b] = ff_prod(u.r, v.i);
+                        im[2 * b + 1] = ff_prod(ui, v.r);
+                    }
+                    w[s][a] = {((re[0] + re[1]) + (re[2] + re[3])) + (re[4] + re[5]),
+                               ((im[0] + im[1]) + (im[2] + im[3])) + (im[4] + im[5])};
+                }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    cx<T> z = {T(0), T(0)};
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[s][b], z) : cfmaconj(U[b][a], h[s][b], z);
+                    w[s][a] = z;
+                }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             reconstruct<MU, S>(acc[r][c], acc[r][3 + c], acc[r][6 + c], acc[r][9 + c], w[0][c], w[1][c]);

@@ -30,6 +30,79 @@ struct cx {
     T r, i;
 };
 
+// ---------------------------------------------------------- float-float --
+// A float-float number hi + lo (|lo| <= half an ulp of hi) carries about 48
+// significant bits, enough for FP64-class accuracy, with FP32 arithmetic only:
+// Knuth's error-free two-sum, the FMA-based exact product of two floats
+// (Dekker's product without splitting) and the usual renormalisation
+// (double-float arithmetic as in Dekker 1971 and the QD / DSFUN libraries).
+// On GB300 the FP32 pipes issue 64 times as many operations per cycle as the
+// FP64 pipe, so a stencil in this arithmetic outruns native FP64 several-fold.
+// The _rn intrinsics keep the compiler from contracting the error-free steps
+// into fused multiply-adds, which would change what they compute.
+struct ff {
+    float hi, lo;
+    ff() = default;
+    __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr ff(int v) : hi(float(v)), lo(0.f) {}
+    __host__ __device__ constexpr ff(float v) : hi(v), lo(0.f) {}
+    __device__ ff(double v) : hi(float(v)), lo(float(v - double(float(v)))) {}
+};
+
+// s + e = a + b exactly
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s + e = a + b exactly, given |a| >= |b| (or a = 0)
+__device__ __forceinline__ void ff_fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator+(ff a, ff b)
+{
+    float s, e;
+    ff_two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    ff_fast_two_sum(s, e, s, e);
+    return ff(s, e);
+}
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+// a * b + (cross terms): exact product of the high parts as (p, e), with the
+// two cross products folded into e (|e| ~ 2^-24 |p|; the sloppy addition
+// below accepts such an unnormalised pair)
+__device__ __forceinline__ ff ff_prod(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff(p, e);
+}
+
+// the float and double fma stay visible next to the float-float one
+using ::fma;
+
+// c + a * b: exact product of the high parts, cross terms in FP32, one
+// renormalised sum
+__device__ __forceinline__ ff fma(ff a, ff b, ff c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float s, t;
+    ff_two_sum(p, c.hi, s, t);
+    t = __fadd_rn(t, __fadd_rn(e, c.lo));
+    ff_fast_two_sum(s, t, s, t);
+    return ff(s, t);
+}
+
 template <typename T>
 __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return {a.r + b.r, a.i + b.i}; }
 template <typename T>
@@ -136,6 +209,33 @@ struct SpF32 {
         float2 *p = static_cast<float2 *>(base);
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[k * vh + i] = make_float2(float(v[k].r), float(v[k].i));
+    }
+};
+
+// FP64-class spinor in float-float: 12 planes of the high parts, then 12 of
+// the low parts (192 bytes per site, as FP64).
+struct SpFF {
+    using real = ff;
+    static constexpr int kBytesPerSite = 192;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> v[12])
+    {
+        const float2 *p = static_cast<const float2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float2 h = ld_keep(p + k * vh + i), l = ld_keep(p + (12 + k) * vh + i);
+            v[k] = {ff(h.x, l.x), ff(h.y, l.y)};
+        }
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i, const cx<ff> v[12])
+    {
+        float2 *p = static_cast<float2 *>(base);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            p[k * vh + i] = make_float2(v[k].r.hi, v[k].i.hi);
+            p[(12 + k) * vh + i] = make_float2(v[k].r.lo, v[k].i.lo);
+        }
     }
 };
 
@@ -387,6 +487,39 @@ struct Lk16_12 {
         uint4 *p = static_cast<uint4 *>(base);
         p[i] = make_uint4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<uint2 *>(p + vh)[i] = make_uint2(w[4], w[5]);
+    }
+};
+
+// FP64-class links in float-float: the high parts in the LkF32_18 layout,
+// then the low parts in the same layout (144 bytes per site, as FP64).
+struct LkFF18 {
+    static constexpr int kBytesPerSite = 144;
+    template <typename R>
+    __device__ static __forceinline__ void load(const void *base, long long vh, long long i,
+                                                cx<R> U[3][3])
+    {
+        cx<float> H[3][3], L[3][3];
+        LkF32_18T<>::load(base, vh, i, H);
+        LkF32_18T<>::load(static_cast<const char *>(base) + 72 * vh, vh, i, L);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) U[a][b] = {ff(H[a][b].r, L[a][b].r), ff(H[a][b].i, L[a][b].i)};
+    }
+    __device__ static __forceinline__ void store(void *base, long long vh, long long i,
+                                                 const cx<double> U[3][3])
+    {
+        cx<double> H[3][3], L[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const ff r(U[a][b].r), m(U[a][b].i);
+                H[a][b] = {double(r.hi), double(m.hi)};
+                L[a][b] = {double(r.lo), double(m.lo)};
+            }
+        LkF32_18T<>::store(base, vh, i, H);
+        LkF32_18T<>::store(static_cast<char *>(base) + 72 * vh, vh, i, L);
     }
 };
 

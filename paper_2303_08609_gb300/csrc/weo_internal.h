@@ -28,6 +28,10 @@ int fail_cuda(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 
 // ----------------------------------------------------------------- formats --
+// Internal operator precision next to weo_prec: float-float arithmetic with
+// 18-real links (FP64-class accuracy from FP32 operations); spinors SpFF.
+constexpr int kPrecFF = 4;
+
 // Spinor storage kinds inside the library.
 enum SpinorKind { SK_F64 = 0, SK_F32 = 1, SK_H16 = 2, SK_B16 = 3 };
 
@@ -40,6 +44,7 @@ inline long long link_site_bytes(int prec, int fmt)
     const bool c = fmt == WEO_LINK12;
     switch (prec) {
     case WEO_F64: return c ? 96 : 144;
+    case kPrecFF: return 144;
     case WEO_F32: return c ? 48 : 72;
     default: return c ? 24 : 36;
     }
@@ -84,13 +89,15 @@ struct wilson_eo_s {
     weo::PackedGauge gauge;      // in the handle's precision
     weo::PackedGauge gauge_f64;  // solver: true residual (lazy)
     weo::PackedGauge gauge_lo;   // solver: inner operator of an FP64 handle (lazy)
+    weo::PackedGauge gauge_ff;   // float-float operator (lazy)
+    weo::Buffer ff_in, ff_out, ff_tmp;  // float-float spinors of wilson_eo_apply_ff64
     weo::Buffer canon_gauge;     // device copy of the canonical field (kept for lazy packs)
     int canon_is_f64 = 1;
     weo::Buffer tmp;             // odd-site intermediate of M_eo
     weo::Buffer tmp2, tmp3;      // odd-site fields of the link gradient
     weo::Buffer even1;           // even-site field (force: 2 M_eo phi)
     weo::Buffer stage_in, stage_out, stage_aux;
-    weo::LaunchCfg cfg[4];       // per spinor precision kind
+    weo::LaunchCfg cfg[5];       // per operator precision (weo_prec, then kPrecFF)
     weo::Profiler *prof = nullptr;
     weo::SolverState *solver = nullptr;
     // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
@@ -116,6 +123,7 @@ int launch_hop(int prec, int fmt, int io, bool dag, bool axpy, const HopParams &
                const LaunchCfg &cfg, cudaStream_t s);
 int launch_hop_f64(int fmt, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
                    cudaStream_t s);
+int launch_hop_ff(bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg, cudaStream_t s);
 int launch_hop_f32(int fmt, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
                    cudaStream_t s);
 int launch_hop_h16(int fmt, int io, bool dag, bool axpy, const HopParams &p, const LaunchCfg &cfg,
@@ -159,7 +167,8 @@ int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b
                  cudaStream_t user);
 int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs);
 int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi_applies,
-                 double *seconds);
+                 int *ff_applies, double *seconds);
+int solver_residual_mode(wilson_eo_s *h, int mode);
 void solver_destroy(wilson_eo_s *h);
 int prepare_source_device(wilson_eo_s *h, void *rhs_e, const void *eta_e, const void *eta_o,
                           cudaStream_t s);
@@ -170,6 +179,10 @@ int solve_full_device(wilson_eo_s *h, void *xi_e, void *xi_o, const void *eta_e,
                       int *iters_out, double *relres_out, cudaStream_t user);
 
 // Pack a canonical gauge field (device memory) into `g` (allocates).
+// ff.cu: complex128 <-> float-float spinors (nrhs x V/2 sites), float-float gauge
+int ff_from_f64(void *dst, const void *src, long long vh, int nrhs, cudaStream_t s);
+int ff_to_f64(void *dst, const void *src, long long vh, int nrhs, cudaStream_t s);
+int ff_gauge(wilson_eo_s *h, const PackedGauge **g, cudaStream_t s);
 int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *canon, int is_f64,
                cudaStream_t s);
 

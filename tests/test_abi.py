@@ -111,3 +111,8 @@ def test_alu_peak_rejects_other_precisions(lib):
 
 def test_rhs_lanes_rejects_bad_values(lib):
     assert lib.wilson_eo_set_rhs_lanes(None, 2) == -1
+
+
+def test_ff_and_residual_mode_reject_null(lib):
+    assert lib.wilson_eo_apply_ff64(None, None, None, 1, 0, None) == -1
+    assert lib.wilson_eo_solver_residual(None, 1) == -1
