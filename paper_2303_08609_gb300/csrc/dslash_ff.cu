@@ -14,6 +14,38 @@
 
 namespace weo {
 
+// a + b without the final renormalisation: the sum of the high parts is
+// error-free and its error joins the low parts. hi + lo keeps the value to
+// ~2^-44 relative to the operands even when lo is no longer below half an ulp
+// of hi, which the next operations accept; the accumulators are renormalised
+// once at the end.
+__device__ __forceinline__ ff ff_add_nr(ff a, ff b)
+{
+    float s, e;
+    ff_two_sum(a.hi, b.hi, s, e);
+    return ff(s, __fadd_rn(__fadd_rn(a.lo, b.lo), e));
+}
+__device__ __forceinline__ cx<ff> cadd_nr(cx<ff> a, cx<ff> b) { return {ff_add_nr(a.r, b.r), ff_add_nr(a.i, b.i)}; }
+
+// sum of the exact products (p_k, e_k) as in the twice-working-precision dot
+// product of Ogita, Rump and Oishi (2005): the p_k are added with error-free
+// two-sums, every rounding error and every e_k is collected in FP32, and the
+// result is renormalised once
+template <int N>
+__device__ __forceinline__ ff ff_sum_products(const ff (&t)[N])
+{
+    float s = t[0].hi, err = t[0].lo;
+#pragma unroll
+    for (int k = 1; k < N; ++k) {
+        float e;
+        ff_two_sum(s, t[k].hi, s, e);
+        err = __fadd_rn(err, __fadd_rn(e, t[k].lo));
+    }
+    float hi, lo;
+    ff_two_sum(s, err, hi, lo);  // s may have cancelled below err
+    return ff(hi, lo);
+}
+
 // z * c for a unit c: rot selects c = +-i (else +-1), neg the sign
 __device__ __forceinline__ cx<ff> unit_mul(cx<ff> z, bool rot, bool neg)
 {
@@ -110,8 +142,8 @@ __device__ __forceinline__ void hop_site_ff(const HopParams &p, const int i, con
         for (int col = 0; col < 3; ++col) {
             const cx<ff> a0 = unit_mul(c.j0 == 2 ? v[6 + col] : v[9 + col], c.rot0, c.neg0);
             const cx<ff> a1 = unit_mul(c.j1 == 2 ? v[6 + col] : v[9 + col], c.rot1, c.neg1);
-            h[0][col] = cadd(v[col], a0);
-            h[1][col] = cadd(v[3 + col], a1);
+            h[0][col] = cadd_nr(v[col], a0);
+            h[1][col] = cadd_nr(v[3 + col], a1);
         }
         // w = U h: six exact real products per component, summed pairwise
 #pragma unroll
@@ -127,19 +159,26 @@ __device__ __forceinline__ void hop_site_ff(const HopParams &p, const int i, con
                     im[2 * b] = ff_prod(U[a][b].r, h[s][b].i);
                     im[2 * b + 1] = ff_prod(U[a][b].i, h[s][b].r);
                 }
-                w[a] = {((re[0] + re[1]) + (re[2] + re[3])) + (re[4] + re[5]),
-                        ((im[0] + im[1]) + (im[2] + im[3])) + (im[4] + im[5])};
+                w[a] = {ff_sum_products(re), ff_sum_products(im)};
             }
             // out_s += w ; out_{2,3} += d w for the spin row whose k equals s
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                acc[3 * s + a] = cadd(acc[3 * s + a], w[a]);
-                if (c.k2 == s) acc[6 + a] = cadd(acc[6 + a], unit_mul(w[a], c.rot2, c.neg2));
-                if (c.k3 == s) acc[9 + a] = cadd(acc[9 + a], unit_mul(w[a], c.rot3, c.neg3));
+                acc[3 * s + a] = cadd_nr(acc[3 * s + a], w[a]);
+                if (c.k2 == s) acc[6 + a] = cadd_nr(acc[6 + a], unit_mul(w[a], c.rot2, c.neg2));
+                if (c.k3 == s) acc[9 + a] = cadd_nr(acc[9 + a], unit_mul(w[a], c.rot3, c.neg3));
             }
         }
     }
 
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {  // renormalise the accumulators (hi may have cancelled)
+        float hi, lo;
+        ff_two_sum(acc[k].r.hi, acc[k].r.lo, hi, lo);
+        acc[k].r = ff(hi, lo);
+        ff_two_sum(acc[k].i.hi, acc[k].i.lo, hi, lo);
+        acc[k].i = ff(hi, lo);
+    }
     if (Axpy) {
         cx<ff> xv[12];
         SpFF::load(static_cast<const char *>(p.x) + rhs * p.x_stride, p.vh, i, xv);
@@ -153,6 +192,8 @@ __device__ __forceinline__ void hop_site_ff(const HopParams &p, const int i, con
     SpFF::store(static_cast<char *>(p.out) + rhs * p.out_stride, p.vh, i, acc);
 }
 
+// three CTAs of 128 threads per SM (168 registers, no spills): measured
+// 2.17 TFlop/s at 32^3 x 64 against 1.97 / 2.11 / 1.81 for two, four or five
 template <bool Dag, bool Axpy>
 __global__ void __launch_bounds__(128, 3) hop_kernel_ff(const HopParams p)
 {
