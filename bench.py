@@ -37,7 +37,6 @@ DIMS = (32, 32, 32, 64)
 KAPPA = 0.13
 EPS = 0.4
 FLOP_PER_SITE = 1344  # per M_eo per lattice site
-WORKLOAD = "M_eo^dag M_eo, 32^3x64, FP32, 18-real links, kappa=0.13, exp(i*0.4*H) links"
 
 
 def parse():
@@ -54,6 +53,8 @@ def parse():
     ap.add_argument("--threads", type=int, default=128, help="threads per CTA of the hop kernels")
     ap.add_argument("--order", type=int, default=1,
                     help="1: second hop walks the sites downward (reads the freshest part first)")
+    ap.add_argument("--ff", action="store_true",
+                    help="main step in float-float arithmetic (wilson_eo_apply_ff64, complex128 spinors)")
     ap.add_argument("--no-variants", action="store_true", help="skip the other precisions")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extras", action="store_true",
@@ -67,10 +68,17 @@ def parse():
                     help="lattice extents (default 32 32 32 64, the benchmark workload)")
     args = ap.parse_args()
     if args.dims:
-        global DIMS, WORKLOAD
+        global DIMS
         DIMS = tuple(args.dims)
-        WORKLOAD = WORKLOAD.replace("32^3x64", "x".join(map(str, DIMS)))
     return args
+
+
+def workload_name(args):
+    prec = "float-float (FP64-class)" if args.ff else {"f64": "FP64", "f32": "FP32", "f16": "FP16 storage",
+                                                        "bf16": "BF16 storage"}[args.prec]
+    links = 18 if args.ff else args.linkfmt
+    return (f"M_eo^dag M_eo, {'x'.join(map(str, DIMS))}, {prec}, {links}-real links, "
+            f"kappa={KAPPA}, exp(i*{EPS}*H) links")
 
 
 def dist_env():
@@ -196,7 +204,7 @@ def algo_bytes_per_site(label):
         return 96 / 2 + 4 * lk + 96 / 2
     if label.startswith("hop_f32"):
         sp, lk = 96, (48 if "_l12" in label else 72)
-    elif label.startswith("hop_f64"):
+    elif label.startswith("hop_f64") or label.startswith("hop_ff"):
         sp, lk = 192, (96 if "_l12" in label else 144)
     elif label.startswith("hop_to16"):
         lk = 24 if "_l12" in label else 36
@@ -239,7 +247,7 @@ def run_ours(args, rank, world, local):
     vh = V // 2
     # the handle's spinor dtype: complex128 for FP64 handles, complex64 otherwise
     x_host = np.ascontiguousarray(np.moveaxis(psi, 0, -1)).astype(
-        np.complex128 if args.prec == "f64" else np.complex64)
+        np.complex128 if args.prec == "f64" or args.ff else np.complex64)
     x = torch.from_numpy(x_host).to(dev)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
@@ -251,8 +259,12 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        weo.wilson_eo_apply(op.handle, y, x, 1, stream)
-        weo.wilson_eo_apply_dag(op.handle, z, y, 1, stream)
+        if args.ff:
+            weo.wilson_eo_apply_ff64(op.handle, y, x, 1, False, stream)
+            weo.wilson_eo_apply_ff64(op.handle, z, y, 1, True, stream)
+        else:
+            weo.wilson_eo_apply(op.handle, y, x, 1, stream)
+            weo.wilson_eo_apply_dag(op.handle, z, y, 1, stream)
 
     def barrier():
         if world > 1:
@@ -299,6 +311,8 @@ def run_ours(args, rank, world, local):
     hops = {k: round((1368 if "_axpy" in k else 1320) * (V // 2) / (ms / cnt * 1e-3) / 1e9, 1)
             for k, (ms, cnt) in prof.items()}
     useful = useful_bytes_per_site(args.prec, args.linkfmt)
+    link_bytes = 144 if args.ff else {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[args.prec]
+    links_mb = 4 * V * (link_bytes * 2 // 3 if args.linkfmt == 12 and not args.ff else link_bytes) / 1e6
     roofline = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1),
                 "peak": peak, "peak_source": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -349,8 +363,12 @@ def run_ours(args, rank, world, local):
     def e2e_steps(count, nstreams):
         for k in range(count):
             j = k % nstreams
-            weo.wilson_eo_apply(ops2[j].handle, ys[j], xh[j], 1, streams[j])
-            weo.wilson_eo_apply_dag(ops2[j].handle, zh[j], ys[j], 1, streams[j])
+            if args.ff:
+                weo.wilson_eo_apply_ff64(ops2[j].handle, ys[j], xh[j], 1, False, streams[j])
+                weo.wilson_eo_apply_ff64(ops2[j].handle, zh[j], ys[j], 1, True, streams[j])
+            else:
+                weo.wilson_eo_apply(ops2[j].handle, ys[j], xh[j], 1, streams[j])
+                weo.wilson_eo_apply_dag(ops2[j].handle, zh[j], ys[j], 1, streams[j])
 
     ke = max(6, min(400, args.steps // 4))
     e2e_ms = {}
@@ -478,15 +496,17 @@ def run_ours(args, rank, world, local):
             "metric": METRIC, "value": round(value, 1), "unit": "GFlop/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f32": "f32", "f64": "f64", "f16": "f16-storage/f32",
+            "dtype": "float-float (2 x f32)" if args.ff else
+                     {"f32": "f32", "f64": "f64", "f16": "f16-storage/f32",
                       "bf16": "bf16-storage/f32"}[args.prec],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA,
+            "config": {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
                        "links": f"exp(i*{EPS}*H), {args.linkfmt}-real", "prec": args.prec,
                        "flop_per_site_per_meo": FLOP_PER_SITE,
                        "algo": "fused" if args.algo else "two hop launches",
                        "threads": args.threads, "second_hop_order": "down" if args.order else "up",
-                       "l2": "inputs larger than L2 (604 MB of links per hop pass)",
+                       "l2": f"inputs larger than L2 ({links_mb:.0f} MB of links per hop pass)"
+                             if links_mb > 129 else f"links {links_mb:.0f} MB per hop pass (L2 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gflops_1368_per_site": round(value * 1368 / FLOP_PER_SITE, 1),
             "roofline": roofline, "hop_gflops": hops, "cpu_baseline": cpu, "e2e": e2e,
@@ -792,7 +812,7 @@ def run_reference(args, rank, world, local):
            "n_gpus": world, "steps": args.steps, "warmup": max(1, args.warmup),
            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "lattice": list(DIMS), "kappa": KAPPA,
+           "config": {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
                       "sample_lattice": list(sd)},
            "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s",
                             "cores": oracle.get_threads(), "kind": "oracle", "sample": sample,
