@@ -407,7 +407,8 @@ void solver_destroy(wilson_eo_s *h)
     if (S->stream) cudaStreamDestroy(S->stream);
     if (S->host) cudaFreeHost(S->host);
     Buffer *bufs[] = {&S->scal, &S->x64, &S->b64, &S->r64, &S->e64, &S->t64, &S->odd64,
-                      &S->xs, &S->rs, &S->p, &S->Ap, &S->t32, &S->oddlo, &S->p64, &S->Ap64};
+                      &S->xs, &S->rs, &S->p, &S->Ap, &S->t32, &S->oddlo, &S->p64, &S->Ap64,
+                      &S->xff, &S->eff, &S->tff, &S->oddff};
     for (Buffer *b : bufs) b->release();
     delete S;
     h->solver = nullptr;
