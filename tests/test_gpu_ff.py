@@ -101,3 +101,24 @@ def test_mixed_solve_with_ff_residuals(weo, oracle_lib, prec):
     assert res[1]["fp64_applies"] <= 2 and res[0]["ff_applies"] == 0
     assert res[0]["fp64_applies"] == res[0]["reliable_updates"] + 1
     assert abs(res[1]["iterations"] - res[0]["iterations"]) <= 16
+
+
+def test_handle_releases_float_float_fields(weo):
+    """Device memory taken by the float-float gauge field, work fields and the
+    solver's float-float vectors comes back when the handle is destroyed."""
+    import torch
+
+    dims = (16, 16, 16, 16)
+    U = to_device(gen.gauge_field(dims, "haar", seed=137))
+    b = to_device(to_planar(gen.gaussian_spinor(dims, seed=138)[0]), "f64")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        op = weo.WilsonEO(dims, 0.12, U, prec="f16")
+        op.apply_ff64(b)
+        x, info = op.solve(b, tol=1e-10, mixed=True)
+        assert info["converged"] and info["ff_applies"] >= 1
+        del x
+        op.close()
+    torch.cuda.synchronize()
+    assert free0 - torch.cuda.mem_get_info()[0] < 64 << 20
