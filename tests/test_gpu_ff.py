@@ -113,7 +113,7 @@ def test_handle_releases_float_float_fields(weo):
     b = to_device(to_planar(gen.gaussian_spinor(dims, seed=138)[0]), "f64")
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
-    for _ in range(2):
+    for _ in range(3):  # a leak of the solver's float-float fields alone is 25 MB a round
         op = weo.WilsonEO(dims, 0.12, U, prec="f16")
         op.apply_ff64(b)
         x, info = op.solve(b, tol=1e-10, mixed=True)
@@ -121,4 +121,4 @@ def test_handle_releases_float_float_fields(weo):
         del x
         op.close()
     torch.cuda.synchronize()
-    assert free0 - torch.cuda.mem_get_info()[0] < 64 << 20
+    assert free0 - torch.cuda.mem_get_info()[0] < 32 << 20
