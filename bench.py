@@ -645,16 +645,20 @@ def multi_solve_comparison(U, dev):
             b[3 * s_ + c, s_, c, site] = 1.0
     Ud = torch.from_numpy(U).to(dev)
     res = {"lattice": list(DIMS), "kappa": KAPPA, "nrhs": 12, "tol": 1e-10}
-    for name, prec, mixed, rb in (("mixed_f16", "f16", True, 4), ("mixed_f32", "f32", True, 4),
-                                  ("plain_f64", "f64", False, 1)):
+    for name, prec, mixed in (("mixed_f16", "f16", True), ("mixed_f32", "f32", True),
+                              ("plain_f64", "f64", False)):
         op = weo.WilsonEO(DIMS, KAPPA, Ud, prec=prec)
-        if rb > 1:
-            weo.wilson_eo_set_launch(op.handle, 128, rb)
+        # the operator's launch configuration for 12 right-hand sides, tuned
+        weo.wilson_eo_tune(op.handle, nrhs=12)
+        threads, rb, lanes = weo.wilson_eo_get_launch(op.handle)
+        cfg = dict(weo.wilson_eo_get_algorithm(op.handle), threads=threads, rhs_per_thread=rb,
+                   rhs_lanes=lanes)
         try:
             x, info = op.solve(b, tol=1e-10, maxiter=20000, mixed=mixed)
             res[name] = {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
                          "reliable_updates": info["reliable_updates"],
-                         "max_true_relres": max(info["true_relres"]), "converged": info["converged"]}
+                         "max_true_relres": max(info["true_relres"]), "converged": info["converged"],
+                         "tuned": cfg}
             del x
         except weo.WilsonEOError as exc:
             res[name] = {"error": str(exc)}

@@ -290,8 +290,10 @@ int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *lookahead, int *threa
  * those calls are invalid); clears the record. WEO_OK otherwise. */
 int wilson_eo_check(wilson_eo_t h, void *stream);
 
-/* Current launch configuration of the handle's hopping kernels. */
-int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block);
+/* Current launch configuration of the handle's hopping kernels: threads per
+ * CTA, right-hand sides per thread, right-hand sides on neighbouring lanes
+ * (wilson_eo_set_launch, wilson_eo_set_rhs_lanes). Any pointer may be NULL. */
+int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block, int *lanes);
 
 /* The hopping term of wilson_eo_hop computed as on `ranks` sub-domains of the
  * lattice split along t (ranks divides Lt), with every t-hop that crosses a

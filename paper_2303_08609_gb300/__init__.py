@@ -91,7 +91,7 @@ def _load():
         "wilson_eo_apply_batch_rhs": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
                                           ctypes.POINTER(P), IP, I, P]),
         "wilson_eo_tune": (I, [P, I, IP, IP, ctypes.POINTER(D), P]),
-        "wilson_eo_get_launch": (I, [P, IP, IP]),
+        "wilson_eo_get_launch": (I, [P, IP, IP, IP]),
         "wilson_eo_set_algorithm": (I, [P, I, I, I]),
         "wilson_eo_check": (I, [P, P]),
         "wilson_eo_hop_split": (I, [P, I, I, I, P, P, P]),
@@ -481,9 +481,11 @@ def wilson_eo_check(h, stream=None):
 
 
 def wilson_eo_get_launch(h):
-    t, r = ctypes.c_int(), ctypes.c_int()
-    _check(_load().wilson_eo_get_launch(h, ctypes.byref(t), ctypes.byref(r)), "wilson_eo_get_launch")
-    return t.value, r.value
+    """(threads per CTA, right-hand sides per thread, right-hand-side lanes)."""
+    t, r, l = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_load().wilson_eo_get_launch(h, ctypes.byref(t), ctypes.byref(r), ctypes.byref(l)),
+           "wilson_eo_get_launch")
+    return t.value, r.value, l.value
 
 
 def wilson_eo_destroy(h):

@@ -207,11 +207,12 @@ extern "C" int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rh
     }
 }
 
-extern "C" int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block)
+extern "C" int wilson_eo_get_launch(wilson_eo_t h, int *threads, int *rhs_block, int *lanes)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
     if (threads) *threads = h->cfg[h->prec].threads;
     if (rhs_block) *rhs_block = h->cfg[h->prec].rhs_block;
+    if (lanes) *lanes = h->cfg[h->prec].lanes;
     return WEO_OK;
 }
 
