@@ -695,12 +695,13 @@ def solve_comparison(dev, dims, only=None):
                                     ("mixed_bf16_fused", "bf16", True, 1),
                                     ("mixed_f32_fused", "f32", True, 1),
                                     ("mixed_f16_two_pass", "f16", True, 0),
+                                    ("mixed_f16_l12_two_pass", "f16", True, 0),
                                     ("mixed_f16_two_pass_fp64res", "f16", True, 0),
                                     ("mixed_f16_two_pass_delta0.03", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0)):
         if only and name not in only:
             continue
-        op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=18)
+        op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=12 if "_l12" in name else 18)
         if algo:
             weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
         if "delta" in name:
