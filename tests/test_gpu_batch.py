@@ -252,3 +252,26 @@ def test_batch_multi_rhs_mixed_lattices(weo, oracle_lib, prec):
                 assert rel_l2(got[r], want[r]) <= TOL[prec]
     for o in ops:
         o.close()
+
+
+def test_batch_rhs_rejects_bad_counts(weo):
+    """nrhs per lattice outside 1..1024 is refused by the library before any launch
+    (called through the raw C ABI: the binding would refuse 1025 on array size)."""
+    import ctypes
+
+    import torch
+
+    dims = (4, 4, 4, 4)
+    U = to_device(gen.gauge_field(dims, "haar", seed=34))
+    op = weo.WilsonEO(dims, 0.12, U, prec="f32")
+    x = torch.zeros((2, 4, 3, op.vh), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    P = ctypes.c_void_p
+    hs = (P * 1)(op.handle.value if isinstance(op.handle, ctypes.c_void_p) else op.handle)
+    outs = (P * 1)(y.data_ptr())
+    ins = (P * 1)(x.data_ptr())
+    for bad in (0, 1025, -1):
+        rs = (ctypes.c_int * 1)(bad)
+        assert weo.library().wilson_eo_apply_batch_rhs(1, hs, outs, ins, rs, 0, None) == -1
+        assert "nrhs" in weo.wilson_eo_last_error()
+    op.close()

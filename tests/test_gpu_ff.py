@@ -128,3 +128,18 @@ def test_handle_releases_float_float_fields(weo):
         round_trip()
     torch.cuda.synchronize()
     assert free0 - torch.cuda.mem_get_info()[0] < 32 << 20
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 4, 2, 6), (6, 2, 4, 2)])
+def test_ff_smallest_lattices(weo, oracle_lib, dims):
+    """Extents of 2 (every neighbour pair wraps onto the same site) and Lx = 2."""
+    U = gen.gauge_field(dims, "haar", seed=139)
+    psi = gen.gaussian_spinor(dims, nrhs=2, seed=140)
+    op = weo.WilsonEO(dims, 0.12, to_device(U), prec="f64")
+    x = to_device(to_planar(psi), "f64")
+    for dag in (False, True):
+        y = op.apply_ff64(x, dag=dag)
+        f = oracle_lib.meo_dag if dag else oracle_lib.meo
+        for r in range(2):
+            assert rel_l2(from_planar(y[r].cpu().numpy()), f(U, 0.12, psi[r], dims)) <= 1e-13
+    op.close()
