@@ -509,6 +509,7 @@ def run_ours(args, rank, world, local):
                              if links_mb > 129 else f"links {links_mb:.0f} MB per hop pass (L2 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "gflops_1368_per_site": round(value * 1368 / FLOP_PER_SITE, 1),
+            "site_updates_per_s": round(world * 2 * V / (ms_step * 1e-3), 0),
             "roofline": roofline, "hop_gflops": hops, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(), "check": check, "alu_peaks": alu_peaks, "variants": variants,
