@@ -13,13 +13,14 @@
 // The force of S = |M_eo phi|^2 (g = 2 M_eo phi) is F = TA(G U^dag),
 // TA(W) = (W - W^dag)/2 - tr(W - W^dag)/6: the traceless anti-Hermitian matrix
 // with dS/d eps = Re tr(X^dag F) under U -> exp(eps X) U.
+#include <type_traits>
+
 #include "weo_internal.h"
 
 namespace weo {
 
 struct GradParams {
     int lxh, ly, lz, lt, vh;
-    int parity;            // parity of the link base sites x handled by this launch
     const void *g, *phi;   // even
     const void *t, *w;     // odd
     const char *gauge;     // packed links (for the force)
@@ -29,11 +30,33 @@ struct GradParams {
     int force;             // 0: gradient, 1: TA(G U^dag)
 };
 
-template <int MU, int S, typename T>
-__device__ __forceinline__ void proj_all(const cx<T> v[12], cx<T> h[2][3])
+constexpr int kGradThreads = 128;
+
+// The projection of the hopping kernel written as h = psi_up + S q, with q
+// fixed by mu (chiral basis): the sign S may then differ between threads.
+template <int MU, typename T>
+__device__ __forceinline__ void proj_rt(const cx<T> v[12], T S, cx<T> h[2][3])
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
+    for (int c = 0; c < 3; ++c) {
+        const cx<T> p2 = v[6 + c], p3 = v[9 + c];
+        cx<T> q0, q1;
+        if (MU == 0) {
+            q0 = cmuli(p3);
+            q1 = cmuli(p2);
+        } else if (MU == 1) {
+            q0 = p3;
+            q1 = cneg(p2);
+        } else if (MU == 2) {
+            q0 = cmuli(p2);
+            q1 = cneg(cmuli(p3));
+        } else {
+            q0 = cneg(p2);
+            q1 = cneg(p3);
+        }
+        h[0][c] = {fma(S, q0.r, v[c].r), fma(S, q0.i, v[c].i)};
+        h[1][c] = {fma(S, q1.r, v[3 + c].r), fma(S, q1.i, v[3 + c].i)};
+    }
 }
 
 // G[a][b] += sum_r hp[r][a] conj(hq[r][b])
@@ -49,49 +72,40 @@ __device__ __forceinline__ void outer_acc(cx<T> G[3][3], const cx<T> hp[2][3], c
         }
 }
 
+// The 3x3 result for link (mu, x) of a thread's site: the gradient G, or the
+// force TA(G U^dag), as 18 reals in m.
 template <class Sp, class Lk, int MU>
-__device__ __forceinline__ void grad_dir(const GradParams &p, long long i, long long nb,
-                                         const cx<typename Sp::real> own0[12],
-                                         const cx<typename Sp::real> own1[12], long long lex)
+__device__ __forceinline__ void grad_link(const GradParams &p, int par, long long i, long long nb,
+                                          const cx<typename Sp::real> own0[12],
+                                          const cx<typename Sp::real> own1[12],
+                                          typename Sp::real m[18])
 {
     using T = typename Sp::real;
+    // even x: G = (1-g)g(x) (x) (1-g)t(x+mu) + (1+g)phi(x) (x) (1+g)w(x+mu);
+    // odd x:  G = (1+g)t(x) (x) (1+g)g(x+mu) + (1-g)w(x) (x) (1-g)phi(x+mu)
+    const T S1 = par ? T(-1) : T(1);
     cx<T> n0[12], n1[12], ha[2][3], hb[2][3];
+    Sp::load(par ? p.g : p.t, p.vh, nb, n0);
+    Sp::load(par ? p.phi : p.w, p.vh, nb, n1);
     cx<T> G[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) G[a][b] = {T(0), T(0)};
-    if (p.parity == 0) {
-        // own0 = g(x), own1 = phi(x); neighbours t(x+mu), w(x+mu)
-        Sp::load(p.t, p.vh, nb, n0);
-        Sp::load(p.w, p.vh, nb, n1);
-        proj_all<MU, 1>(own0, ha);   // (1 - gamma) g(x)
-        proj_all<MU, 1>(n0, hb);     // same projector on t(x+mu)
-        outer_acc(G, ha, hb);
-        proj_all<MU, -1>(own1, ha);  // (1 + gamma) on phi(x)
-        proj_all<MU, -1>(n1, hb);    // (1 + gamma) w(x+mu)
-        outer_acc(G, ha, hb);
-    } else {
-        // own0 = t(x), own1 = w(x); neighbours g(x+mu), phi(x+mu)
-        Sp::load(p.g, p.vh, nb, n0);
-        Sp::load(p.phi, p.vh, nb, n1);
-        proj_all<MU, -1>(own0, ha);  // (1 + gamma) on t(x)
-        proj_all<MU, -1>(n0, hb);    // (1 + gamma) g(x+mu)
-        outer_acc(G, ha, hb);
-        proj_all<MU, 1>(own1, ha);   // (1 - gamma) w(x)
-        proj_all<MU, 1>(n1, hb);     // (1 - gamma) on phi(x+mu)
-        outer_acc(G, ha, hb);
-    }
+    proj_rt<MU>(own0, S1, ha);
+    proj_rt<MU>(n0, S1, hb);
+    outer_acc(G, ha, hb);
+    proj_rt<MU>(own1, -S1, ha);
+    proj_rt<MU>(n1, -S1, hb);
+    outer_acc(G, ha, hb);
     const T sc = T(p.scale);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) G[a][b] = cscale(G[a][b], sc);
-    const long long V = 2LL * p.vh;
-    T *out = static_cast<T *>(p.out) + 18 * (MU * V + lex);
     if (p.force) {
         cx<T> U[3][3];
-        Lk::load(p.gauge + (2 * MU + p.parity) * p.gauge_pb, p.vh, i, U);
+        Lk::load(p.gauge + (2 * MU + par) * p.gauge_pb, p.vh, i, U);
         cx<T> W[3][3];  // G U^dag
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -108,71 +122,94 @@ __device__ __forceinline__ void grad_dir(const GradParams &p, long long i, long 
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                T re = (W[a][b].r - W[b][a].r) * T(0.5);
-                T im = (W[a][b].i + W[b][a].i) * T(0.5) - (a == b ? trim : T(0));
-                out[2 * (3 * a + b)] = re;
-                out[2 * (3 * a + b) + 1] = im;
+                m[2 * (3 * a + b)] = (W[a][b].r - W[b][a].r) * T(0.5);
+                m[2 * (3 * a + b) + 1] = (W[a][b].i + W[b][a].i) * T(0.5) - (a == b ? trim : T(0));
             }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                out[2 * (3 * a + b)] = G[a][b].r;
-                out[2 * (3 * a + b) + 1] = G[a][b].i;
+                m[2 * (3 * a + b)] = G[a][b].r;
+                m[2 * (3 * a + b) + 1] = G[a][b].i;
             }
     }
 }
 
-// One thread per site of parity p.parity; it writes the four links based there.
+// Stage the block's matrices for one direction in shared memory and write them
+// out as one contiguous, coalesced range of the canonical [mu][lex] array.
+template <typename T>
+__device__ __forceinline__ void write_links(const GradParams &p, int mu, long long lex0, int nvalid,
+                                            const T m[18], T *sh)
+{
+#pragma unroll
+    for (int k = 0; k < 18; ++k) sh[threadIdx.x * 18 + k] = m[k];
+    __syncthreads();
+    const long long V = 2LL * p.vh;
+    T *dst = static_cast<T *>(p.out) + 18 * (mu * V + lex0);
+    if (nvalid == kGradThreads && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        // 16-byte vectors: 18 * kGradThreads reals per block (the block's range
+        // starts 16-byte aligned whenever the output array does)
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        constexpr int kPer = 16 / sizeof(T);
+        const V4 *src4 = reinterpret_cast<const V4 *>(sh);
+        V4 *dst4 = reinterpret_cast<V4 *>(dst);
+        for (int k = threadIdx.x; k < 18 * kGradThreads / kPer; k += kGradThreads) dst4[k] = src4[k];
+    } else {
+        for (int k = threadIdx.x; k < 18 * nvalid; k += kGradThreads) dst[k] = sh[k];
+    }
+    __syncthreads();
+}
+
+// One thread per lattice site (lexicographic, both parities): it computes the
+// four links based there; each block writes its links per direction as one
+// contiguous range.
 template <class Sp, class Lk>
-__global__ void __launch_bounds__(128) link_grad_kernel(const GradParams p)
+__global__ void __launch_bounds__(kGradThreads) link_grad_kernel(const GradParams p)
 {
     using T = typename Sp::real;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.vh) return;
-    int rem = i;
-    const int xh = rem % p.lxh;
-    rem /= p.lxh;
-    const int y = rem % p.ly;
-    rem /= p.ly;
-    const int z = rem % p.lz;
-    const int t = rem / p.lz;
-    const int par = (y + z + t + p.parity) & 1;
-    const int x = 2 * xh + par;
-    const long long lx = 2LL * p.lxh;
-    const long long lex = ((long long)(t * p.lz + z) * p.ly + y) * lx + x;
-    const int sy = p.lxh, sz = p.lxh * p.ly, st = p.lxh * p.ly * p.lz;
-    const int xp = par ? (xh + 1 == p.lxh ? 0 : xh + 1) : xh;
-    const long long n_x = i - xh + xp;
-    const long long n_y = i + (y + 1 == p.ly ? -(p.ly - 1) * sy : sy);
-    const long long n_z = i + (z + 1 == p.lz ? -(p.lz - 1) * sz : sz);
-    const long long n_t = i + (t + 1 == p.lt ? -(long long)(p.lt - 1) * st : st);
+    __shared__ __align__(16) T sh[18 * kGradThreads];
+    const long long lx = 2LL * p.lxh, V = 2LL * p.vh;
+    const long long lex0 = (long long)blockIdx.x * kGradThreads;
+    const long long lex = lex0 + threadIdx.x;
+    const int nvalid = (int)(V - lex0 < kGradThreads ? V - lex0 : kGradThreads);
+    const bool valid = lex < V;
+    long long r = valid ? lex : 0;
+    const int x = (int)(r % lx);
+    r /= lx;
+    const int y = (int)(r % p.ly);
+    r /= p.ly;
+    const int z = (int)(r % p.lz);
+    const int t = (int)(r / p.lz);
+    const int par = (x + y + z + t) & 1;
+    const long long i = (valid ? lex : 0) >> 1;
+    // compact indices of x + mu (the other parity)
+    const long long base = ((long long)(t * p.lz + z) * p.ly + y) * lx;
+    const long long n_x = (base + (x + 1 == lx ? 0 : x + 1)) >> 1;
+    const long long n_y = (((long long)(t * p.lz + z) * p.ly + (y + 1 == p.ly ? 0 : y + 1)) * lx + x) >> 1;
+    const long long n_z = (((long long)(t * p.lz + (z + 1 == p.lz ? 0 : z + 1)) * p.ly + y) * lx + x) >> 1;
+    const long long n_t = (((long long)((t + 1 == p.lt ? 0 : t + 1) * p.lz + z) * p.ly + y) * lx + x) >> 1;
     cx<T> own0[12], own1[12];
-    if (p.parity == 0) {
-        Sp::load(p.g, p.vh, i, own0);
-        Sp::load(p.phi, p.vh, i, own1);
-    } else {
-        Sp::load(p.t, p.vh, i, own0);
-        Sp::load(p.w, p.vh, i, own1);
-    }
-    grad_dir<Sp, Lk, 0>(p, i, n_x, own0, own1, lex);
-    grad_dir<Sp, Lk, 1>(p, i, n_y, own0, own1, lex);
-    grad_dir<Sp, Lk, 2>(p, i, n_z, own0, own1, lex);
-    grad_dir<Sp, Lk, 3>(p, i, n_t, own0, own1, lex);
+    // own fields: g, phi on even sites; t, w on odd sites
+    Sp::load(par ? p.t : p.g, p.vh, i, own0);
+    Sp::load(par ? p.w : p.phi, p.vh, i, own1);
+    T m[18];
+    grad_link<Sp, Lk, 0>(p, par, i, n_x, own0, own1, m);
+    write_links(p, 0, lex0, nvalid, m, sh);
+    grad_link<Sp, Lk, 1>(p, par, i, n_y, own0, own1, m);
+    write_links(p, 1, lex0, nvalid, m, sh);
+    grad_link<Sp, Lk, 2>(p, par, i, n_z, own0, own1, m);
+    write_links(p, 2, lex0, nvalid, m, sh);
+    grad_link<Sp, Lk, 3>(p, par, i, n_t, own0, own1, m);
+    write_links(p, 3, lex0, nvalid, m, sh);
 }
 
 template <class Sp, class Lk>
-static int launch_grad(const GradParams &p0, cudaStream_t s)
+static int launch_grad(const GradParams &p, cudaStream_t s)
 {
-    const int threads = 128;
-    const unsigned blocks = (unsigned)((p0.vh + threads - 1) / threads);
-    for (int par = 0; par < 2; ++par) {
-        GradParams p = p0;
-        p.parity = par;
-        link_grad_kernel<Sp, Lk><<<blocks, threads, 0, s>>>(p);
-        WEO_CUDA(cudaGetLastError());
-    }
+    const unsigned blocks = (unsigned)((2LL * p.vh + kGradThreads - 1) / kGradThreads);
+    link_grad_kernel<Sp, Lk><<<blocks, kGradThreads, 0, s>>>(p);
+    WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
 
@@ -204,7 +241,6 @@ int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, 
     p.lz = h->dims[2];
     p.lt = h->dims[3];
     p.vh = (int)h->vh;
-    p.parity = 0;
     p.g = g;
     p.phi = phi;
     p.t = h->tmp2.ptr;
