@@ -530,10 +530,10 @@ int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi
         WEO_TRY(stage_out(h->stage_aux, force, gb, &out, &out_host));
         if (dS_dphi_e) WEO_TRY(stage_out(h->stage_out, dS_dphi_e, sb, &dphi, &dphi_host));
         WEO_TRY(h->even1.ensure(sb));
-        // g = dS/dchi = 2 M_eo phi
+        // g = dS/dchi = 2 M_eo phi; its first hop leaves t = H_oe phi in h->tmp
         WEO_TRY(meo_device(h, h->even1.ptr, phi, 1, false, s));
         WEO_TRY(scale_spinor(h, h->even1.ptr, 1, 2.0, s));
-        WEO_TRY(link_grad_device(h, out, h->even1.ptr, phi, 1, s));
+        WEO_TRY(link_grad_device(h, out, h->even1.ptr, phi, 1, s, h->tmp.ptr));
         if (dphi) WEO_TRY(meo_device(h, dphi, h->even1.ptr, 1, true, s));  // 2 M^dag M phi
         if (dphi) WEO_TRY(finish_out(dS_dphi_e, dphi, sb, dphi_host, s));
         return finish_out(force, out, gb, out_host, s);

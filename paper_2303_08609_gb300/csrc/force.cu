@@ -216,7 +216,7 @@ static int launch_grad(const GradParams &p, cudaStream_t s)
 // Gradient (force = 0) or force (force = 1) with g and phi on the device.
 // Uses h->tmp2 and h->tmp3 for t and w (odd).
 int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, int force,
-                     cudaStream_t s)
+                     cudaStream_t s, const void *t_known)
 {
     const long long ext = h->vh * (h->prec == WEO_F64 ? 192 : 96);
     WEO_TRY(h->tmp2.ensure((size_t)ext));
@@ -226,11 +226,13 @@ int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, 
     hp.gauge = static_cast<const char *>(h->gauge.buf.ptr);
     hp.gauge_pb = h->gauge.pb;
     hp.in_stride = hp.out_stride = ext;
-    // t = H_oe phi
+    // t = H_oe phi (unless the caller has it: the intermediate of M_eo phi)
     hp.out_parity = 1;
-    hp.in = phi;
-    hp.out = h->tmp2.ptr;
-    WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, false, false, hp, s));
+    if (!t_known) {
+        hp.in = phi;
+        hp.out = h->tmp2.ptr;
+        WEO_TRY(handle_hop(h, h->prec, h->fmt, IO_SAME, false, false, hp, s));
+    }
     // w = H_eo^dag g: the adjoint hop onto odd sites
     hp.in = g;
     hp.out = h->tmp3.ptr;
@@ -243,7 +245,7 @@ int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, 
     p.vh = (int)h->vh;
     p.g = g;
     p.phi = phi;
-    p.t = h->tmp2.ptr;
+    p.t = t_known ? t_known : h->tmp2.ptr;
     p.w = h->tmp3.ptr;
     p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
     p.gauge_pb = h->gauge.pb;

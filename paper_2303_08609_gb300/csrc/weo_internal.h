@@ -158,7 +158,7 @@ int hop_split_device(wilson_eo_s *h, int ranks, int out_parity, bool dag, void *
 int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s);
 // link gradient (force = 0) or force TA(G U^dag) (force = 1), force.cu
 int link_grad_device(wilson_eo_s *h, void *out, const void *g, const void *phi, int force,
-                     cudaStream_t s);
+                     cudaStream_t s, const void *t_known = nullptr);
 int scale_spinor(wilson_eo_s *h, void *v, int nrhs, double c, cudaStream_t s);
 
 // solver.cu
