@@ -282,6 +282,32 @@ int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads)
  * hangs; the context stays usable. FP32 / 16-bit handles, device arrays. */
 int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e, void *stream);
 
+/* Hopping kernel fed by TMA (Eq. 1 for one parity, as wilson_eo_hop; used by
+ * every hop of M_eo, M_eo^dag, the solvers and the force whose spinors are FP32
+ * with 18-real FP32 links and one right-hand side). staged = 1: the output
+ * sites are cut into tiles of R lattice rows; one producer warp per CTA loads
+ * each tile's neighbour-spinor rows (same plane, y-1 / y+R rows, planes z+-1
+ * and t+-1), its eight link rows and the axpy addend as cp.async.bulk.tensor
+ * boxes into a three-stage shared-memory ring, and twelve consumer warps compute
+ * from shared memory. Same arithmetic per direction as the default kernel; the
+ * x/y and z/t halves of the sum are added at the end, so results agree to
+ * FP32 rounding, not bitwise. Needs Lx/2 even and some R >= 2 dividing Ly with
+ * R * Lx/2 <= 64 (WEO_ERR_UNSUPPORTED otherwise); arrays whose addresses are
+ * not 16-byte aligned fall back to the default kernel. Waits are bounded
+ * (about a second); a wait that gives up is reported by wilson_eo_check as
+ * WEO_ERR_TIMEOUT. staged = 0 (default) restores the default kernel. */
+int wilson_eo_set_staging(wilson_eo_t h, int staged);
+int wilson_eo_get_staging(wilson_eo_t h, int *staged);
+
+/* Failure-path test of the staged hop: one hop D_oe (in_e even, out_o odd,
+ * device arrays, FP32 18-real handle on an eligible lattice) whose producer
+ * never loads the first tile of each CTA and whose wait limit is 2 ms: the
+ * consumers of that stage give up, the producer then gives up waiting for them
+ * and waits for its own loads in flight, every CTA returns, and wilson_eo_check
+ * reports WEO_ERR_TIMEOUT. out_o receives partial garbage. Nothing faults,
+ * traps or hangs; the context stays usable. */
+int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e, void *stream);
+
 /* Current algorithm (0 two launches, 1 fused), fused lookahead and threads. */
 int wilson_eo_get_algorithm(wilson_eo_t h, int *algo, int *lookahead, int *threads);
 

@@ -96,6 +96,9 @@ def _load():
         "wilson_eo_check": (I, [P, P]),
         "wilson_eo_hop_split": (I, [P, I, I, I, P, P, P]),
         "wilson_eo_inject_fused_timeout": (I, [P, P, P, P]),
+        "wilson_eo_set_staging": (I, [P, ctypes.c_int]),
+        "wilson_eo_get_staging": (I, [P, IP]),
+        "wilson_eo_inject_staged_timeout": (I, [P, P, P, P]),
         "wilson_eo_get_algorithm": (I, [P, IP, IP, IP]),
         "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
         "wilson_eo_alu_peak": (I, [I, ctypes.POINTER(D), P]),
@@ -474,6 +477,24 @@ def wilson_eo_inject_fused_timeout(h, out_e, in_e, stream=None):
     _expect(h, (out_e, in_e), 1, where="wilson_eo_inject_fused_timeout")
     _check(_load().wilson_eo_inject_fused_timeout(h, _ptr(out_e), _ptr(in_e), _stream(stream)),
            "wilson_eo_inject_fused_timeout")
+
+
+def wilson_eo_set_staging(h, staged=True):
+    """Hops of FP32 18-real operators fed by TMA through a shared-memory ring
+    (True) or the default one-site-per-thread kernel (False)."""
+    _check(_load().wilson_eo_set_staging(h, int(bool(staged))), "wilson_eo_set_staging")
+
+
+def wilson_eo_get_staging(h):
+    v = ctypes.c_int()
+    _check(_load().wilson_eo_get_staging(h, ctypes.byref(v)), "wilson_eo_get_staging")
+    return bool(v.value)
+
+
+def wilson_eo_inject_staged_timeout(h, out_o, in_e, stream=None):
+    _expect(h, (out_o, in_e), 1, where="wilson_eo_inject_staged_timeout")
+    _check(_load().wilson_eo_inject_staged_timeout(h, _ptr(out_o), _ptr(in_e), _stream(stream)),
+           "wilson_eo_inject_staged_timeout")
 
 
 def wilson_eo_check(h, stream=None):

@@ -144,12 +144,18 @@ static int upload_gauge(wilson_eo_s *h, const void *gauge, int gauge_is_f64, cud
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
                cudaStream_t s)
 {
+    const bool staged = h->cfg[prec].staged && prec == WEO_F32 && fmt == WEO_LINK18 &&
+                        io == IO_SAME && p.nrhs == 1 && staged_arrays_ok(p, axpy);
     int tok = -1;
     if (h->prof) {
-        const char *kind = io == IO_TO16 ? "hop_to16" : io == IO_FROM16 ? "hop_from16" : "hop";
+        const char *kind = staged ? "hop_staged"
+                           : io == IO_TO16   ? "hop_to16"
+                           : io == IO_FROM16 ? "hop_from16"
+                                             : "hop";
         tok = prof_begin(h, kernel_label(kind, prec, fmt, dag, axpy).c_str(), s);
     }
-    int st = launch_hop(prec, fmt, io, dag, axpy, p, h->cfg[prec], s);
+    int st = staged ? launch_hop_staged(h, dag, axpy, p, s)
+                    : launch_hop(prec, fmt, io, dag, axpy, p, h->cfg[prec], s);
     prof_end(h, tok, s);
     return st;
 }
@@ -371,6 +377,56 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
     return WEO_OK;
 }
 
+int wilson_eo_set_staging(wilson_eo_t h, int staged)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        if (staged != 0 && staged != 1) return set_error(WEO_ERR_ARG, "staged must be 0 or 1");
+        if (staged && !staged_eligible(h))
+            return set_error(WEO_ERR_UNSUPPORTED,
+                             "staged hop: needs Lx/2 even, R | Ly for some R >= 2 with R Lx/2 <= 64");
+        DeviceGuard dg(h->device);
+        if (staged) WEO_TRY(fused_prepare(h, 0));  // error word of the bounded waits
+        h->cfg[WEO_F32].staged = staged;
+        return WEO_OK;
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_set_staging");
+    }
+}
+
+int wilson_eo_get_staging(wilson_eo_t h, int *staged)
+{
+    if (!h || !staged) return set_error(WEO_ERR_ARG, "NULL handle or pointer");
+    *staged = h->cfg[WEO_F32].staged;
+    return WEO_OK;
+}
+
+int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e, void *stream)
+{
+    try {
+        if (!h || !out_o || !in_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
+        if (h->prec != WEO_F32 || h->fmt != WEO_LINK18 || !staged_eligible(h))
+            return set_error(WEO_ERR_UNSUPPORTED, "staged hop: FP32 18-real handle on an eligible lattice");
+        if (!is_device_pointer(out_o) || !is_device_pointer(in_e))
+            return set_error(WEO_ERR_ARG, "device arrays only");
+        DeviceGuard dg(h->device);
+        WEO_TRY(fused_prepare(h, static_cast<cudaStream_t>(stream)));
+        HopParams p = geom_params(h);
+        p.nrhs = 1;
+        p.gauge = static_cast<const char *>(h->gauge.buf.ptr);
+        p.gauge_pb = h->gauge.pb;
+        p.out_parity = 1;
+        p.in = in_e;
+        p.in_stride = h->vh * 96;
+        p.out = out_o;
+        p.out_stride = h->vh * 96;
+        if (!staged_arrays_ok(p, false)) return set_error(WEO_ERR_ARG, "arrays must be 16-byte aligned");
+        return launch_hop_staged(h, false, false, p, static_cast<cudaStream_t>(stream), true);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_staged_timeout");
+    }
+}
+
 int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
@@ -409,7 +465,7 @@ int wilson_eo_check(wilson_eo_t h, void *stream)
         DeviceGuard dg(h->device);
         unsigned int err = 0;
         WEO_TRY(fused_take_error(h, static_cast<cudaStream_t>(stream), &err));
-        if (err) return set_error(WEO_ERR_TIMEOUT, "a bounded wait in the fused M_eo kernel gave up; results of the calls since the last check are invalid");
+        if (err) return set_error(WEO_ERR_TIMEOUT, "a bounded wait in the fused M_eo or staged hop kernel gave up; results of the calls since the last check are invalid");
         return WEO_OK;
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_check");

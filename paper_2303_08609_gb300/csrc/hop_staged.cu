@@ -1,0 +1,586 @@
+// Hopping kernel with its operands staged in shared memory by TMA: the same
+// sum as hop_kernel (Eq. 1 for one parity, Sec. 3.3's H_oe / H_eo pass), FP32
+// spinors and 18-real FP32 links, one right-hand side.
+//
+// The output sites are cut into tiles of R lattice rows: R * Lx/2 consecutive
+// compact indices inside one (z, t) plane. Everything the hopping sum of a tile
+// reads is then a few rectangular boxes of the planar arrays:
+//   input spinor (parity 1-p): the tile rows of the same plane (+-x, and +-y
+//     inside the tile), the rows y0-1 and y0+R (periodic in y), and the tile
+//     rows of the planes z+1, z-1, t+1, t-1 (periodic);
+//   links: U_mu(x) at the tile (the four fields of parity p); U_mu(x-mu) of
+//     parity 1-p at the tile rows of the same plane (mu = x), of the planes
+//     z-1 and t-1, and for mu = y at row y0-1 (periodic) and rows y0..y0+R-2;
+//   the axpy addend at the tile.
+// One producer warp issues them as cp.async.bulk.tensor loads into a ring of
+// three stages, each with an mbarrier that counts the bytes landed; twelve
+// consumer warps in three groups (one per stage) compute from shared memory
+// only, so the bytes in flight no longer depend on the registers each
+// thread holds. In a group, two warps take the x and y directions and two the
+// z and t directions of 2 x 32 sites; the z/t partial sums are handed over in
+// shared memory (in the slots of the z+1 spinor rows they no longer need).
+//
+// Every wait is bounded (a time limit on the global timer): on expiry the
+// kernel records an error word that wilson_eo_check reports, stops, and the
+// producer waits, again bounded, for its own copies still in flight.
+#include <cuda.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "weo_internal.h"
+
+namespace weo {
+
+namespace {
+
+constexpr int kStages = 3;                         // ring depth = consumer groups
+constexpr int kConsumerWarps = 4 * kStages;
+constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
+constexpr int kMaxTile = 64;                       // sites per tile (box limits)
+
+// shared-memory regions of one stage, byte offsets
+struct StageLayout {
+    int sp[7];      // spinor: tile rows, row y0-1, row y0+R, planes z+1, z-1, t+1, t-1
+    int lf4[4], lf2[4];  // forward links U_mu(x): float4 part, float2 part
+    int lb4[4], lb2[4];  // backward links of x, z, t (index 1 unused)
+    int ya4, ya2, yb4, yb2;  // backward y links: row y0-1, rows y0..y0+R-2
+    int x;          // axpy addend
+    int bytes;      // size of one stage
+    int tx;         // bytes the TMA loads of one tile deliver
+};
+
+struct StagedParams {
+    CUtensorMap sp_tile, sp_row, x_tile;
+    CUtensorMap lk4_tile, lk4_row, lk4_rest;
+    CUtensorMap lk2_tile, lk2_row, lk2_rest;
+    StageLayout L;
+    int lxh, ly, lz, lt, rows, tile, ntiles, out_parity, reverse;
+    long long vh;
+    float a;
+    float2 *out;
+    unsigned int *err;
+    unsigned long long limit_ns;
+    int inject;  // failure-path test: the producer never loads the CTA's first tile
+};
+
+int round128(int b) { return (b + 127) & ~127; }
+
+bool make_layout(int lxh, int rows, bool axpy, StageLayout &L)
+{
+    const int T = lxh * rows;
+    int off = 0;
+    auto take = [&](int bytes) {
+        const int o = off;
+        off += round128(bytes);
+        return o;
+    };
+    L.sp[0] = take(96 * T);
+    L.sp[1] = take(96 * lxh);
+    L.sp[2] = take(96 * lxh);
+    for (int k = 3; k < 7; ++k) L.sp[k] = take(96 * T);
+    for (int mu = 0; mu < 4; ++mu) {
+        L.lf4[mu] = take(64 * T);
+        L.lf2[mu] = take(8 * T);
+    }
+    L.lb4[1] = L.lb2[1] = 0;
+    for (int mu : {0, 2, 3}) {
+        L.lb4[mu] = take(64 * T);
+        L.lb2[mu] = take(8 * T);
+    }
+    L.ya4 = take(64 * lxh);
+    L.ya2 = take(8 * lxh);
+    L.yb4 = take(64 * (rows - 1) * lxh);
+    L.yb2 = take(8 * (rows - 1) * lxh);
+    L.x = axpy ? take(96 * T) : 0;
+    L.bytes = off;
+    L.tx = 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + (axpy ? 96 * T : 0);
+    return kStages * L.bytes + 16 * 8 * kStages <= 227 * 1024;
+}
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of `bar` with the given parity to complete, at most
+// limit_ns nanoseconds; false (and the error word set) on expiry
+__device__ __noinline__ bool mbar_wait(uint64_t *bar, unsigned parity, const StagedParams &P)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > P.limit_ns) {
+            atomicOr(P.err, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                       uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_2d_hint(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            uint64_t *bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_3d_hint(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar)),
+        "l"(pol)
+        : "memory");
+}
+
+// ---------------------------------------------------------------- tiles --
+struct TileGeo {
+    int plane, y0, z, t;
+    long long i0;  // first compact index of the tile
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const StagedParams &P, int j)
+{
+    if (P.reverse) j = P.ntiles - 1 - j;
+    TileGeo g;
+    const int row0 = j * P.rows;
+    g.plane = row0 / P.ly;
+    g.y0 = row0 - g.plane * P.ly;
+    g.z = g.plane % P.lz;
+    g.t = g.plane / P.lz;
+    g.i0 = (long long)row0 * P.lxh;
+    return g;
+}
+
+// compact index of row y of plane (z, t)
+__device__ __forceinline__ int row_start(const StagedParams &P, int z, int t, int y)
+{
+    return ((t * P.lz + z) * P.ly + y) * P.lxh;
+}
+
+// issue the loads of tile j into the stage at `base`
+template <bool Axpy>
+__device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *base, uint64_t *full,
+                                           uint64_t pol)
+{
+    const TileGeo g = tile_geo(P, j);
+    const StageLayout &L = P.L;
+    const int ly = P.ly, lz = P.lz, lt = P.lt;
+    const int ym = g.y0 == 0 ? ly - 1 : g.y0 - 1;
+    const int yp = g.y0 + P.rows == ly ? 0 : g.y0 + P.rows;
+    const int zp = g.z + 1 == lz ? 0 : g.z + 1, zm = g.z == 0 ? lz - 1 : g.z - 1;
+    const int tp = g.t + 1 == lt ? 0 : g.t + 1, tm = g.t == 0 ? lt - 1 : g.t - 1;
+    const int i0 = (int)g.i0;
+    const int i_ym = row_start(P, g.z, g.t, ym);
+    const int i_zm = row_start(P, zm, g.t, g.y0), i_tm = row_start(P, g.z, tm, g.y0);
+    mbar_expect_tx(full, (unsigned)L.tx);
+    // input spinor (parity 1-p); the coordinate is in floats, 2 per complex
+    tma_2d(base + L.sp[0], &P.sp_tile, 2 * i0, 0, full);
+    tma_2d(base + L.sp[1], &P.sp_row, 2 * i_ym, 0, full);
+    tma_2d(base + L.sp[2], &P.sp_row, 2 * row_start(P, g.z, g.t, yp), 0, full);
+    tma_2d(base + L.sp[3], &P.sp_tile, 2 * row_start(P, zp, g.t, g.y0), 0, full);
+    tma_2d(base + L.sp[4], &P.sp_tile, 2 * i_zm, 0, full);
+    tma_2d(base + L.sp[5], &P.sp_tile, 2 * row_start(P, g.z, tp, g.y0), 0, full);
+    tma_2d(base + L.sp[6], &P.sp_tile, 2 * i_tm, 0, full);
+    // links (field 2 mu + parity); read once per launch, so evict first
+    const int op = P.out_parity, ip = op ^ 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        tma_3d_hint(base + L.lf4[mu], &P.lk4_tile, 4 * i0, 0, 2 * mu + op, full, pol);
+        tma_2d_hint(base + L.lf2[mu], &P.lk2_tile, 2 * i0, 2 * mu + op, full, pol);
+    }
+    tma_3d_hint(base + L.lb4[0], &P.lk4_tile, 4 * i0, 0, ip, full, pol);
+    tma_2d_hint(base + L.lb2[0], &P.lk2_tile, 2 * i0, ip, full, pol);
+    tma_3d_hint(base + L.lb4[2], &P.lk4_tile, 4 * i_zm, 0, 4 + ip, full, pol);
+    tma_2d_hint(base + L.lb2[2], &P.lk2_tile, 2 * i_zm, 4 + ip, full, pol);
+    tma_3d_hint(base + L.lb4[3], &P.lk4_tile, 4 * i_tm, 0, 6 + ip, full, pol);
+    tma_2d_hint(base + L.lb2[3], &P.lk2_tile, 2 * i_tm, 6 + ip, full, pol);
+    tma_3d_hint(base + L.ya4, &P.lk4_row, 4 * i_ym, 0, 2 + ip, full, pol);
+    tma_2d_hint(base + L.ya2, &P.lk2_row, 2 * i_ym, 2 + ip, full, pol);
+    tma_3d_hint(base + L.yb4, &P.lk4_rest, 4 * i0, 0, 2 + ip, full, pol);
+    tma_2d_hint(base + L.yb2, &P.lk2_rest, 2 * i0, 2 + ip, full, pol);
+    if (Axpy) tma_2d(base + L.x, &P.x_tile, 2 * i0, 0, full);
+}
+
+// one hopping direction from shared memory: spinor planes of stride `ss`
+// (complex) at index si, link planes of stride `ls` at index li
+template <int MU, bool FWD, int S0>
+__device__ __forceinline__ void staged_dir(cx<float> (&acc)[12], const float2 *sp, int ss, int si,
+                                           const float4 *l4, const float2 *l2, int ls, int li)
+{
+    constexpr int S = FWD ? S0 : -S0;
+    const float4 a = l4[li], b = l4[ls + li], c = l4[2 * ls + li], d = l4[3 * ls + li];
+    const float2 e = l2[li];
+    cx<float> U[3][3];
+    U[0][0] = {a.x, a.y};
+    U[0][1] = {a.z, a.w};
+    U[0][2] = {b.x, b.y};
+    U[1][0] = {b.z, b.w};
+    U[1][1] = {c.x, c.y};
+    U[1][2] = {c.z, c.w};
+    U[2][0] = {d.x, d.y};
+    U[2][1] = {d.z, d.w};
+    U[2][2] = {e.x, e.y};
+    cx<float> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const float2 q = sp[k * ss + si];
+        v[k] = {q.x, q.y};
+    }
+    cx<float> h[2][3];
+#pragma unroll
+    for (int col = 0; col < 3; ++col)
+        project<MU, S>(v[col], v[3 + col], v[6 + col], v[9 + col], h[0][col], h[1][col]);
+    cx<float> w[2][3];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            cx<float> zz = {0.f, 0.f};
+#pragma unroll
+            for (int col = 0; col < 3; ++col)
+                zz = FWD ? cfma(U[r][col], h[s][col], zz) : cfmaconj(U[col][r], h[s][col], zz);
+            w[s][r] = zz;
+        }
+#pragma unroll
+    for (int col = 0; col < 3; ++col)
+        reconstruct<MU, S>(acc[col], acc[3 + col], acc[6 + col], acc[9 + col], w[0][col], w[1][col]);
+}
+
+template <bool Dag, bool Axpy>
+__global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __grid_constant__ StagedParams P)
+{
+    extern __shared__ __align__(128) char smem[];
+    const StageLayout &L = P.L;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * L.bytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *ready = empty + kStages;  // [stage][half]
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int ntile_cta =
+        P.ntiles > (int)blockIdx.x ? (P.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 2);
+            mbar_init(ready + 2 * s, 1);
+            mbar_init(ready + 2 * s + 1, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {  // producer
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();
+        int issued = 0;
+        for (int k = 0; k < ntile_cta; ++k) {
+            const int s = k % kStages, n = k / kStages;
+            if (n >= 1 && !mbar_wait(empty + s, (unsigned)((n - 1) & 1), P)) break;
+            if (P.inject && k == 0) continue;  // nothing loaded, nothing in flight
+            issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + s * L.bytes,
+                             full + s, pol);
+            issued = k + 1;
+        }
+        // the last loads of each stage must have landed before the CTA exits
+        for (int k = issued - 1; k >= 0 && k >= issued - kStages; --k) {
+            if (P.inject && k == 0) continue;
+            mbar_wait(full + k % kStages, (unsigned)((k / kStages) & 1), P);
+        }
+        return;
+    }
+
+    // consumers: group g owns stage g and the CTA's tiles k = g, g + 3, ...
+    const int g = warp >> 2, q = (warp >> 1) & 1, half = warp & 1;
+    const int s = half * 32 + lane;  // site within the tile
+    const bool active = s < P.tile;
+    const int lxh = P.lxh, T = P.tile;
+    const int r = s / lxh, xh = s - r * lxh;
+    constexpr int S0 = Dag ? -1 : 1;
+    char *base = smem + g * L.bytes;
+    const float2 *sp0 = reinterpret_cast<const float2 *>(base + L.sp[0]);
+    float2 *part = reinterpret_cast<float2 *>(base + L.sp[3]);  // z/t partial sums
+    for (int k = g; k < ntile_cta; k += kStages) {
+        const unsigned par_n = (unsigned)((k / kStages) & 1);
+        if (!mbar_wait(full + g, par_n, P)) return;
+        const TileGeo tg = tile_geo(P, (int)blockIdx.x + k * (int)gridDim.x);
+        cx<float> acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = {0.f, 0.f};
+        if (q == 0) {
+            if (active) {
+                const int y = tg.y0 + r;
+                const int par = (y + tg.z + tg.t + P.out_parity) & 1;
+                const int xp = par ? (xh + 1 == lxh ? 0 : xh + 1) : xh;
+                const int xm = par ? xh : (xh == 0 ? lxh - 1 : xh - 1);
+                const int rb = r * lxh;
+                staged_dir<0, true, S0>(acc, sp0, T, rb + xp,
+                                        reinterpret_cast<const float4 *>(base + L.lf4[0]),
+                                        reinterpret_cast<const float2 *>(base + L.lf2[0]), T, s);
+                staged_dir<0, false, S0>(acc, sp0, T, rb + xm,
+                                         reinterpret_cast<const float4 *>(base + L.lb4[0]),
+                                         reinterpret_cast<const float2 *>(base + L.lb2[0]), T, rb + xm);
+                if (r + 1 < P.rows)
+                    staged_dir<1, true, S0>(acc, sp0, T, rb + lxh + xh,
+                                            reinterpret_cast<const float4 *>(base + L.lf4[1]),
+                                            reinterpret_cast<const float2 *>(base + L.lf2[1]), T, s);
+                else
+                    staged_dir<1, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[2]),
+                                            lxh, xh,
+                                            reinterpret_cast<const float4 *>(base + L.lf4[1]),
+                                            reinterpret_cast<const float2 *>(base + L.lf2[1]), T, s);
+                if (r > 0)
+                    staged_dir<1, false, S0>(acc, sp0, T, rb - lxh + xh,
+                                             reinterpret_cast<const float4 *>(base + L.yb4),
+                                             reinterpret_cast<const float2 *>(base + L.yb2),
+                                             (P.rows - 1) * lxh, rb - lxh + xh);
+                else
+                    staged_dir<1, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[1]),
+                                             lxh, xh, reinterpret_cast<const float4 *>(base + L.ya4),
+                                             reinterpret_cast<const float2 *>(base + L.ya2), lxh, xh);
+            }
+            if (!mbar_wait(ready + 2 * g + half, par_n, P)) return;
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const float2 v = part[c * T + s];
+                    acc[c].r += v.x;
+                    acc[c].i += v.y;
+                }
+                float2 *out = P.out + tg.i0 + s;
+                if (Axpy) {
+                    const float2 *xv = reinterpret_cast<const float2 *>(base + L.x);
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) {
+                        const float2 v = xv[c * T + s];
+                        out[c * P.vh] = make_float2(fmaf(P.a, acc[c].r, v.x), fmaf(P.a, acc[c].i, v.y));
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) out[c * P.vh] = make_float2(acc[c].r, acc[c].i);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + g);
+        } else {
+            if (active) {
+                staged_dir<2, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[3]), T, s,
+                                        reinterpret_cast<const float4 *>(base + L.lf4[2]),
+                                        reinterpret_cast<const float2 *>(base + L.lf2[2]), T, s);
+                staged_dir<2, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[4]), T, s,
+                                         reinterpret_cast<const float4 *>(base + L.lb4[2]),
+                                         reinterpret_cast<const float2 *>(base + L.lb2[2]), T, s);
+                staged_dir<3, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[5]), T, s,
+                                        reinterpret_cast<const float4 *>(base + L.lf4[3]),
+                                        reinterpret_cast<const float2 *>(base + L.lf2[3]), T, s);
+                staged_dir<3, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[6]), T, s,
+                                         reinterpret_cast<const float4 *>(base + L.lb4[3]),
+                                         reinterpret_cast<const float2 *>(base + L.lb2[3]), T, s);
+                // each lane overwrites only the z+1 slots it read itself
+#pragma unroll
+                for (int c = 0; c < 12; ++c) part[c * T + s] = make_float2(acc[c].r, acc[c].i);
+            }
+            // the next TMA load into this stage writes over the partial sums
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ready + 2 * g + half);
+        }
+    }
+}
+
+// -------------------------------------------------------- tensor maps --
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder()
+{
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+// FP32 tensor of rank 2 or 3 (dims[0] contiguous; strides in bytes of dims 1..)
+bool encode(CUtensorMap *m, const void *ptr, int rank, const cuuint64_t *dims,
+            const cuuint64_t *strides, const cuuint32_t *box)
+{
+    EncodeFn fn = encoder();
+    if (!fn) return false;
+    const cuuint32_t one[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(ptr), dims,
+              strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// rows of R per tile: the largest R dividing Ly with R * Lx/2 <= 64, R >= 2
+int staged_rows(int lxh, int ly)
+{
+    if (lxh % 2 != 0) return 0;  // rows must start on 16-byte boundaries
+    for (int r = kMaxTile / lxh; r >= 2; --r)
+        if (ly % r == 0) return r;
+    return 0;
+}
+
+template <bool Dag, bool Axpy>
+int launch_staged(const StagedParams &P, int grid, cudaStream_t s)
+{
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(hop_staged_kernel<Dag, Axpy>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    WEO_CUDA(attr);
+    const size_t bytes = (size_t)kStages * P.L.bytes + 4 * kStages * sizeof(uint64_t);
+    hop_staged_kernel<Dag, Axpy><<<grid, kStagedThreads, bytes, s>>>(P);
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
+}  // namespace
+
+bool staged_eligible(const wilson_eo_s *h)
+{
+    const int lxh = h->dims[0] / 2;
+    StageLayout L;
+    const int rows = staged_rows(lxh, h->dims[1]);
+    // TMA coordinates are 32-bit: 4 floats per site in the link boxes
+    return rows >= 2 && make_layout(lxh, rows, true, L) && 4 * h->vh < (1ll << 31) &&
+           encoder() != nullptr;
+}
+
+bool staged_arrays_ok(const HopParams &p, bool axpy)
+{
+    auto aligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    return aligned(p.in) && aligned(p.gauge) && (!axpy || aligned(p.x)) && (p.gauge_pb & 15) == 0 &&
+           staged_rows(p.lxh, p.ly) >= 2 && 4ll * p.vh < (1ll << 31);
+}
+
+int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
+                      bool inject)
+{
+    const int lxh = p.lxh, rows = staged_rows(lxh, p.ly);
+    if (!staged_arrays_ok(p, axpy) || !h->fused_ctrl.ptr)
+        return set_error(WEO_ERR_UNSUPPORTED, "staged hop: lattice or array alignment not eligible");
+    StagedParams P;
+    std::memset(&P, 0, sizeof(P));
+    if (!make_layout(lxh, rows, axpy, P.L)) return set_error(WEO_ERR_UNSUPPORTED, "staged hop: tile too large");
+    const long long vh = p.vh;
+    const int T = rows * lxh;
+    // spinor: 12 planes of 2 vh floats
+    const cuuint64_t sd[2] = {(cuuint64_t)(2 * vh), 12};
+    const cuuint64_t ss[1] = {(cuuint64_t)(8 * vh)};
+    const cuuint32_t b_tile[2] = {(cuuint32_t)(2 * T), 12}, b_row[2] = {(cuuint32_t)(2 * lxh), 12};
+    // links, float4 part: [field][4 planes][4 vh floats]; float2 part: [field][2 vh floats]
+    const cuuint64_t ld4[3] = {(cuuint64_t)(4 * vh), 4, 8};
+    const cuuint64_t ls4[2] = {(cuuint64_t)(16 * vh), (cuuint64_t)p.gauge_pb};
+    const cuuint64_t ld2[2] = {(cuuint64_t)(2 * vh), 8};
+    const cuuint64_t ls2[1] = {(cuuint64_t)p.gauge_pb};
+    const cuuint32_t b4t[3] = {(cuuint32_t)(4 * T), 4, 1}, b4r[3] = {(cuuint32_t)(4 * lxh), 4, 1},
+                     b4s[3] = {(cuuint32_t)(4 * (rows - 1) * lxh), 4, 1};
+    const cuuint32_t b2t[2] = {(cuuint32_t)(2 * T), 1}, b2r[2] = {(cuuint32_t)(2 * lxh), 1},
+                     b2s[2] = {(cuuint32_t)(2 * (rows - 1) * lxh), 1};
+    const char *lk2 = p.gauge + 64 * vh;
+    bool ok = encode(&P.sp_tile, p.in, 2, sd, ss, b_tile) && encode(&P.sp_row, p.in, 2, sd, ss, b_row) &&
+              encode(&P.lk4_tile, p.gauge, 3, ld4, ls4, b4t) &&
+              encode(&P.lk4_row, p.gauge, 3, ld4, ls4, b4r) &&
+              encode(&P.lk4_rest, p.gauge, 3, ld4, ls4, b4s) &&
+              encode(&P.lk2_tile, lk2, 2, ld2, ls2, b2t) && encode(&P.lk2_row, lk2, 2, ld2, ls2, b2r) &&
+              encode(&P.lk2_rest, lk2, 2, ld2, ls2, b2s);
+    if (ok && axpy) ok = encode(&P.x_tile, p.x, 2, sd, ss, b_tile);
+    if (!ok) return set_error(WEO_ERR_CUDA, "staged hop: tensor map encoding failed");
+    P.lxh = lxh;
+    P.ly = p.ly;
+    P.lz = p.lz;
+    P.lt = p.lt;
+    P.rows = rows;
+    P.tile = T;
+    P.ntiles = (int)(vh / T);
+    P.out_parity = p.out_parity;
+    P.reverse = p.reverse;
+    P.vh = vh;
+    P.a = (float)p.a;
+    P.out = static_cast<float2 *>(p.out);
+    P.err = static_cast<unsigned int *>(h->fused_ctrl.ptr);
+    P.limit_ns = inject ? 2000000ull : 1000000000ull;
+    P.inject = inject ? 1 : 0;
+    int sms = 0;
+    WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int grid = P.ntiles < sms ? P.ntiles : sms;
+    if (dag) return axpy ? launch_staged<true, true>(P, grid, s) : launch_staged<true, false>(P, grid, s);
+    return axpy ? launch_staged<false, true>(P, grid, s) : launch_staged<false, false>(P, grid, s);
+}
+
+}  // namespace weo

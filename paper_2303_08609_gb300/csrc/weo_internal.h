@@ -72,6 +72,7 @@ struct LaunchCfg {
     int threads = 128;
     int rhs_block = 1;   // right-hand sides per thread (register blocking)
     int lanes = 1;       // right-hand sides on neighbouring lanes sharing link loads
+    int staged = 0;      // FP32 18-real, one RHS: operands staged in shared memory by TMA
 };
 
 struct Profiler;
@@ -136,6 +137,13 @@ int prof_begin(wilson_eo_s *h, const char *label, cudaStream_t s);
 void prof_end(wilson_eo_s *h, int token, cudaStream_t s);
 void prof_destroy(wilson_eo_s *h);
 std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axpy);
+
+// hop_staged.cu: the hopping kernel fed by TMA boxes through a ring of
+// shared-memory stages (FP32 spinors, 18-real FP32 links, one right-hand side)
+bool staged_eligible(const wilson_eo_s *h);
+bool staged_arrays_ok(const HopParams &p, bool axpy);
+int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
+                      bool inject = false);
 
 // launch_hop for a handle, with its launch configuration and profiling
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,

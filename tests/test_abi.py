@@ -116,3 +116,9 @@ def test_rhs_lanes_rejects_bad_values(lib):
 def test_ff_and_residual_mode_reject_null(lib):
     assert lib.wilson_eo_apply_ff64(None, None, None, 1, 0, None) == -1
     assert lib.wilson_eo_solver_residual(None, 1) == -1
+
+
+def test_staging_rejects_null_and_bad_values(lib):
+    assert lib.wilson_eo_set_staging(None, 1) == -1
+    assert lib.wilson_eo_get_staging(None, None) == -1
+    assert lib.wilson_eo_inject_staged_timeout(None, None, None, None) == -1

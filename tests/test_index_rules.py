@@ -113,3 +113,126 @@ def test_float_float_projector_table(oracle_lib, mu, S):
     assert np.allclose(full[:2], h)
     # the lower half of (1 - S gamma) psi, rebuilt from h as the kernel does
     assert np.allclose(full[2], d2 * h[k2]) and np.allclose(full[3], d3 * h[k3])
+
+
+# ---------------------------------------------------------------- staged hop --
+# The TMA-staged hopping kernel (csrc/hop_staged.cu) reads every operand of a
+# tile of R rows from boxes it loaded into shared memory. This model follows
+# the kernel's tile, box and in-tile index arithmetic and checks that every
+# value it reads is the neighbour spinor / link the hopping sum needs.
+
+def staged_rows(lxh, ly):
+    if lxh % 2:
+        return 0
+    for r in range(64 // lxh, 1, -1):
+        if ly % r == 0:
+            return r
+    return 0
+
+
+def staged_boxes(dims, rows, j, out_parity):
+    """Boxes of tile j: region -> (array, first compact site, sites, field)."""
+    lx, ly, lz, lt = dims
+    lxh = lx // 2
+    row0 = j * rows
+    plane, y0 = divmod(row0, ly)
+    t, z = divmod(plane, lz)
+
+    def rs(z_, t_, y_):
+        return ((t_ * lz + z_) * ly + y_) * lxh
+
+    ym, yp = (y0 - 1) % ly, (y0 + rows) % ly
+    zp, zm, tp, tm = (z + 1) % lz, (z - 1) % lz, (t + 1) % lt, (t - 1) % lt
+    T, i0, ip = rows * lxh, row0 * lxh, out_parity ^ 1
+    b = {"sp0": ("in", i0, T, None), "sp1": ("in", rs(z, t, ym), lxh, None),
+         "sp2": ("in", rs(z, t, yp), lxh, None), "sp3": ("in", rs(zp, t, y0), T, None),
+         "sp4": ("in", rs(zm, t, y0), T, None), "sp5": ("in", rs(z, tp, y0), T, None),
+         "sp6": ("in", rs(z, tm, y0), T, None)}
+    for mu in range(4):
+        b[f"lf{mu}"] = ("link", i0, T, 2 * mu + out_parity)
+    b["lb0"] = ("link", i0, T, ip)
+    b["lb2"] = ("link", rs(zm, t, y0), T, 4 + ip)
+    b["lb3"] = ("link", rs(z, tm, y0), T, 6 + ip)
+    b["ya"] = ("link", rs(z, t, ym), lxh, 2 + ip)
+    b["yb"] = ("link", i0, (rows - 1) * lxh, 2 + ip)
+    return b, (y0, z, t, i0)
+
+
+def staged_reads(dims, rows, geo, s, out_parity):
+    """(direction, spinor region, index, link region, index) as the consumers read them."""
+    lxh = dims[0] // 2
+    y0, z, t, _ = geo
+    r, xh = divmod(s, lxh)
+    par = (y0 + r + z + t + out_parity) & 1
+    xp = (0 if xh + 1 == lxh else xh + 1) if par else xh
+    xm = xh if par else (lxh - 1 if xh == 0 else xh - 1)
+    rb = r * lxh
+    out = [((0, 1), "sp0", rb + xp, "lf0", s), ((0, -1), "sp0", rb + xm, "lb0", rb + xm)]
+    out.append(((1, 1), "sp0", rb + lxh + xh, "lf1", s) if r + 1 < rows else ((1, 1), "sp2", xh, "lf1", s))
+    out.append(((1, -1), "sp0", rb - lxh + xh, "yb", rb - lxh + xh) if r > 0 else ((1, -1), "sp1", xh, "ya", xh))
+    out += [((2, 1), "sp3", s, "lf2", s), ((2, -1), "sp4", s, "lb2", s),
+            ((3, 1), "sp5", s, "lf3", s), ((3, -1), "sp6", s, "lb3", s)]
+    return out
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 4, 6, 6), (8, 8, 8, 8), (16, 2, 4, 4),
+                                  (12, 6, 4, 8), (4, 6, 2, 22), (32, 8, 2, 4), (24, 8, 2, 2),
+                                  (48, 4, 2, 2)])
+@pytest.mark.parametrize("out_parity", [0, 1])
+@pytest.mark.parametrize("reverse", [False, True])
+def test_staged_tile_reads(dims, out_parity, reverse):
+    lx, ly, lz, lt = dims
+    lxh, vh = lx // 2, lx * ly * lz * lt // 2
+    rows = staged_rows(lxh, ly)
+    assert rows >= 2 and ly % rows == 0
+    T = rows * lxh
+    assert T <= 64 and vh % T == 0
+    ntiles = vh // T
+    seen = np.zeros(vh, dtype=int)
+    for jj in range(ntiles):
+        j = ntiles - 1 - jj if reverse else jj
+        boxes, geo = staged_boxes(dims, rows, j, out_parity)
+        for arr, start, n, field in boxes.values():
+            # every box lies inside its array (TMA would zero-fill, not wrap) and
+            # its x coordinate (floats) is a multiple of 16 bytes
+            assert 0 <= start and start + n <= vh
+            assert (2 * start * 4) % 16 == 0 and (4 * start * 4) % 16 == 0
+            assert 4 * n <= 256 and 2 * n <= 256
+        for s in range(T):
+            i = geo[3] + s
+            seen[i] += 1
+            nb, _ = kernel_neighbours(dims, out_parity, i)
+            for d, sreg, si, lreg, li in staged_reads(dims, rows, geo, s, out_parity):
+                arr, start, n, _ = boxes[sreg]
+                assert 0 <= si < n
+                assert start + si == nb[d], (dims, j, s, d)
+                arr, start, n, field = boxes[lreg]
+                assert 0 <= li < n
+                mu, sgn = d
+                want = (2 * mu + out_parity, i) if sgn > 0 else (2 * mu + (out_parity ^ 1), nb[d])
+                assert (field, start + li) == want, (dims, j, s, d)
+    assert (seen == 1).all()
+
+
+def test_staged_layout_and_byte_count():
+    """Stage regions are 128-byte aligned and disjoint, three stages fit in
+    227 KB for every tile shape the row rule allows, and the mbarrier's expected
+    byte count equals the bytes of the boxes issued."""
+    for lxh in range(2, 33, 2):
+        for ly in range(2, 130, 2):
+            rows = staged_rows(lxh, ly)
+            if rows < 2:
+                continue
+            T = rows * lxh
+            sizes = ([96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [64 * T, 8 * T] * 7 +
+                     [64 * lxh, 8 * lxh, 64 * (rows - 1) * lxh, 8 * (rows - 1) * lxh, 96 * T])
+            off, regions = 0, []
+            for b in sizes:
+                regions.append((off, off + b))
+                off += (b + 127) // 128 * 128
+            assert all(a % 128 == 0 for a, _ in regions)
+            assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
+            fits = 3 * off + 16 * 8 * 3 <= 227 * 1024  # else the plain kernel runs
+            if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)):
+                assert fits, (lxh, ly)
+            assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + 96 * T
