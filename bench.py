@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--algo", type=int, default=0, help="0: two hop launches, 1: fused")
     ap.add_argument("--lookahead", type=int, default=4,
                     help="t-slices the fused kernel's first hop runs ahead of the second")
+    ap.add_argument("--staged", action="store_true",
+                    help="FP32 18-real hops fed by TMA through a shared-memory ring")
     ap.add_argument("--threads", type=int, default=128, help="threads per CTA of the hop kernels")
     ap.add_argument("--order", type=int, default=1,
                     help="1: second hop walks the sites downward (reads the freshest part first)")
@@ -102,7 +104,11 @@ HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "weo_launch.cuh", "dslash_f32
 
 def sources_for(label):
     """Source files a kernel label's code comes from."""
-    return HOP_SOURCES + ("fused.cu",) if label.startswith("fused_") else HOP_SOURCES
+    if label.startswith("fused_"):
+        return HOP_SOURCES + ("fused.cu",)
+    if label.startswith("hop_staged"):
+        return HOP_SOURCES + ("hop_staged.cu",)
+    return HOP_SOURCES
 
 
 def kernel_source_hash(files=HOP_SOURCES):
@@ -202,7 +208,7 @@ def algo_bytes_per_site(label):
         if "_l12" in label:
             lk = lk * 2 // 3
         return 96 / 2 + 4 * lk + 96 / 2
-    if label.startswith("hop_f32"):
+    if label.startswith("hop_f32") or label.startswith("hop_staged_f32"):
         sp, lk = 96, (48 if "_l12" in label else 72)
     elif label.startswith("hop_f64") or label.startswith("hop_ff"):
         sp, lk = 192, (96 if "_l12" in label else 144)
@@ -253,9 +259,15 @@ def run_ours(args, rank, world, local):
     z = torch.empty_like(x)
     op = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec,
                       linkfmt=args.linkfmt)
-    if args.algo:
-        weo.wilson_eo_set_algorithm(op.handle, "fused", args.lookahead, 128)
-    weo.wilson_eo_set_launch(op.handle, args.threads, 1, args.order)
+
+    def configure(o):
+        if args.algo:
+            weo.wilson_eo_set_algorithm(o.handle, "fused", args.lookahead, 128)
+        weo.wilson_eo_set_launch(o.handle, args.threads, 1, args.order)
+        if args.staged:
+            weo.wilson_eo_set_staging(o.handle, True)
+
+    configure(op)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -346,14 +358,10 @@ def run_ours(args, rank, world, local):
     nb = x_host.nbytes
     op2 = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec,
                        linkfmt=args.linkfmt)
-    if args.algo:
-        weo.wilson_eo_set_algorithm(op2.handle, "fused", args.lookahead, 128)
-    weo.wilson_eo_set_launch(op2.handle, args.threads, 1, args.order)
+    configure(op2)
     op3 = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec,
                        linkfmt=args.linkfmt)
-    if args.algo:
-        weo.wilson_eo_set_algorithm(op3.handle, "fused", args.lookahead, 128)
-    weo.wilson_eo_set_launch(op3.handle, args.threads, 1, args.order)
+    configure(op3)
     ops2 = [op, op2, op3]
     streams = [stream, torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
     xh = [torch.from_numpy(x_host).pin_memory() for _ in range(3)]
@@ -404,14 +412,18 @@ def run_ours(args, rank, world, local):
     variants = {}
     if not args.no_variants:
         Ud = torch.from_numpy(U).to(dev)
-        for prec, fmt, algo in (("f32", 12, 0), ("f16", 18, 0), ("f16", 12, 0), ("bf16", 12, 0),
-                                ("f64", 18, 0), ("f32", 18, 1), ("f32", 12, 1), ("f16", 18, 1),
-                                ("f16", 12, 1), ("bf16", 12, 1)):
-            if (prec, fmt, algo) == (args.prec, args.linkfmt, args.algo):
+        # algo 0: two hop launches, 1: fused, 2: two staged (TMA) hop launches
+        main = (args.prec, args.linkfmt, 2 if args.staged else args.algo)
+        for prec, fmt, algo in (("f32", 18, 0), ("f32", 18, 2), ("f32", 12, 0), ("f16", 18, 0),
+                                ("f16", 12, 0), ("bf16", 12, 0), ("f64", 18, 0), ("f32", 18, 1),
+                                ("f32", 12, 1), ("f16", 18, 1), ("f16", 12, 1), ("bf16", 12, 1)):
+            if (prec, fmt, algo) == main:
                 continue
             o2 = weo.WilsonEO(DIMS, KAPPA, Ud, prec=prec, linkfmt=fmt)
-            if algo:
+            if algo == 1:
                 weo.wilson_eo_set_algorithm(o2.handle, "fused", args.lookahead, 128)
+            if algo == 2:
+                weo.wilson_eo_set_staging(o2.handle, True)
             xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev) \
                 if prec == "f64" else x
             yv, zv = torch.empty_like(xv), torch.empty_like(xv)
@@ -446,7 +458,7 @@ def run_ours(args, rank, world, local):
             if yo is not None:
                 ent["meo_rel_l2_64_sites"] = float(np.linalg.norm(yo - want_y)
                                                    / np.linalg.norm(want_y))
-            variants[f"{prec}_l{fmt}" + ("_fused" if algo else "")] = ent
+            variants[f"{prec}_l{fmt}" + ("", "_fused", "_staged")[algo]] = ent
             o2.close()
             del xv, yv, zv
         # float-float M_eo (FP64-class accuracy on the FP32 pipes) on complex128 spinors
@@ -503,7 +515,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
                        "links": f"exp(i*{EPS}*H), {args.linkfmt}-real", "prec": args.prec,
                        "flop_per_site_per_meo": FLOP_PER_SITE,
-                       "algo": "fused" if args.algo else "two hop launches",
+                       "algo": "fused" if args.algo else
+                               "two staged (TMA) hop launches" if args.staged else "two hop launches",
                        "threads": args.threads, "second_hop_order": "down" if args.order else "up",
                        "l2": f"inputs larger than L2 ({links_mb:.0f} MB of links per hop pass)"
                              if links_mb > 129 else f"links {links_mb:.0f} MB per hop pass (L2 129 MB)",
