@@ -52,6 +52,8 @@ def parse():
                     help="t-slices the fused kernel's first hop runs ahead of the second")
     ap.add_argument("--staged", action="store_true",
                     help="FP32 18-real hops fed by TMA through a shared-memory ring")
+    ap.add_argument("--staged-rows", type=int, default=0, help="lattice rows per staged tile (0: auto)")
+    ap.add_argument("--staged-depth", type=int, default=0, help="stages of the staged ring (0: auto)")
     ap.add_argument("--threads", type=int, default=128, help="threads per CTA of the hop kernels")
     ap.add_argument("--order", type=int, default=1,
                     help="1: second hop walks the sites downward (reads the freshest part first)")
@@ -265,7 +267,7 @@ def run_ours(args, rank, world, local):
             weo.wilson_eo_set_algorithm(o.handle, "fused", args.lookahead, 128)
         weo.wilson_eo_set_launch(o.handle, args.threads, 1, args.order)
         if args.staged:
-            weo.wilson_eo_set_staging(o.handle, True)
+            weo.wilson_eo_set_staging(o.handle, True, args.staged_rows, args.staged_depth)
 
     configure(op)
     stream = torch.cuda.current_stream(dev)

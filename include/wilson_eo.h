@@ -295,9 +295,16 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
  * R * Lx/2 <= 64 (WEO_ERR_UNSUPPORTED otherwise); arrays whose addresses are
  * not 16-byte aligned fall back to the default kernel. Waits are bounded
  * (about a second); a wait that gives up is reported by wilson_eo_check as
- * WEO_ERR_TIMEOUT. staged = 0 (default) restores the default kernel. */
-int wilson_eo_set_staging(wilson_eo_t h, int staged);
-int wilson_eo_get_staging(wilson_eo_t h, int *staged);
+ * WEO_ERR_TIMEOUT. staged = 0 (default) restores the default kernel.
+ * rows: lattice rows R per tile (0: the largest that qualifies); depth: stages
+ * of the ring, 2..5 (0: the most up to 3 that fit in 227 KB of shared memory).
+ * A tile of R Lx/2 sites is computed by one or two teams of two warps (x/y and
+ * z/t directions, 32 sites each); six teams share the CTA. */
+int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth);
+
+/* Whether staging is on, and the tile rows and ring depth the handle's lattice
+ * resolves to (0, 0 when it cannot use the staged hop). Pointers may be NULL. */
+int wilson_eo_get_staging(wilson_eo_t h, int *staged, int *rows, int *depth);
 
 /* Failure-path test of the staged hop: one hop D_oe (in_e even, out_o odd,
  * device arrays, FP32 18-real handle on an eligible lattice) whose producer

@@ -96,8 +96,8 @@ def _load():
         "wilson_eo_check": (I, [P, P]),
         "wilson_eo_hop_split": (I, [P, I, I, I, P, P, P]),
         "wilson_eo_inject_fused_timeout": (I, [P, P, P, P]),
-        "wilson_eo_set_staging": (I, [P, ctypes.c_int]),
-        "wilson_eo_get_staging": (I, [P, IP]),
+        "wilson_eo_set_staging": (I, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "wilson_eo_get_staging": (I, [P, IP, IP, IP]),
         "wilson_eo_inject_staged_timeout": (I, [P, P, P, P]),
         "wilson_eo_get_algorithm": (I, [P, IP, IP, IP]),
         "wilson_eo_apply_noalloc": (I, [IP, D, P, P, P, I, P]),
@@ -479,16 +479,21 @@ def wilson_eo_inject_fused_timeout(h, out_e, in_e, stream=None):
            "wilson_eo_inject_fused_timeout")
 
 
-def wilson_eo_set_staging(h, staged=True):
+def wilson_eo_set_staging(h, staged=True, rows=0, depth=0):
     """Hops of FP32 18-real operators fed by TMA through a shared-memory ring
-    (True) or the default one-site-per-thread kernel (False)."""
-    _check(_load().wilson_eo_set_staging(h, int(bool(staged))), "wilson_eo_set_staging")
+    (True) or the default one-site-per-thread kernel (False); rows per tile and
+    ring depth, 0 for automatic."""
+    _check(_load().wilson_eo_set_staging(h, int(bool(staged)), int(rows), int(depth)),
+           "wilson_eo_set_staging")
 
 
 def wilson_eo_get_staging(h):
-    v = ctypes.c_int()
-    _check(_load().wilson_eo_get_staging(h, ctypes.byref(v)), "wilson_eo_get_staging")
-    return bool(v.value)
+    """{"staged": bool, "rows": R, "depth": stages} (rows = depth = 0 when the
+    lattice cannot use the staged hop)."""
+    v, r, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_load().wilson_eo_get_staging(h, ctypes.byref(v), ctypes.byref(r), ctypes.byref(d)),
+           "wilson_eo_get_staging")
+    return {"staged": bool(v.value), "rows": r.value, "depth": d.value}
 
 
 def wilson_eo_inject_staged_timeout(h, out_o, in_e, stream=None):

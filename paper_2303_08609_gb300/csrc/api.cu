@@ -377,14 +377,23 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
     return WEO_OK;
 }
 
-int wilson_eo_set_staging(wilson_eo_t h, int staged)
+int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth)
 {
     try {
         if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
         if (staged != 0 && staged != 1) return set_error(WEO_ERR_ARG, "staged must be 0 or 1");
-        if (staged && !staged_eligible(h))
+        if (rows < 0 || depth < 0 || depth == 1 || depth > 5)
+            return set_error(WEO_ERR_ARG, "rows >= 0, depth 0 or 2..5");
+        const int old_rows = h->staged_rows, old_depth = h->staged_depth;
+        h->staged_rows = rows;
+        h->staged_depth = depth;
+        if (staged && !staged_eligible(h)) {
+            h->staged_rows = old_rows;
+            h->staged_depth = old_depth;
             return set_error(WEO_ERR_UNSUPPORTED,
-                             "staged hop: needs Lx/2 even, R | Ly for some R >= 2 with R Lx/2 <= 64");
+                             "staged hop: needs Lx/2 even and R >= 2 dividing Ly with R Lx/2 <= 64, "
+                             "and the requested stages in 227 KB of shared memory");
+        }
         DeviceGuard dg(h->device);
         if (staged) WEO_TRY(fused_prepare(h, 0));  // error word of the bounded waits
         h->cfg[WEO_F32].staged = staged;
@@ -394,10 +403,14 @@ int wilson_eo_set_staging(wilson_eo_t h, int staged)
     }
 }
 
-int wilson_eo_get_staging(wilson_eo_t h, int *staged)
+int wilson_eo_get_staging(wilson_eo_t h, int *staged, int *rows, int *depth)
 {
-    if (!h || !staged) return set_error(WEO_ERR_ARG, "NULL handle or pointer");
-    *staged = h->cfg[WEO_F32].staged;
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    int r = 0, d = 0;
+    staged_shape(h, &r, &d);
+    if (staged) *staged = h->cfg[WEO_F32].staged;
+    if (rows) *rows = r;
+    if (depth) *depth = d;
     return WEO_OK;
 }
 

@@ -35,10 +35,12 @@ namespace weo {
 
 namespace {
 
-constexpr int kStages = 3;                         // ring depth = consumer groups
-constexpr int kConsumerWarps = 4 * kStages;
+constexpr int kTeams = 6;                        // consumer teams of two warps
+constexpr int kConsumerWarps = 2 * kTeams;
 constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
 constexpr int kMaxTile = 64;                       // sites per tile (box limits)
+constexpr int kMaxStages = 5;
+constexpr int kSmemLimit = 227 * 1024;
 
 // shared-memory regions of one stage, byte offsets
 struct StageLayout {
@@ -57,6 +59,8 @@ struct StagedParams {
     CUtensorMap lk2_tile, lk2_row, lk2_rest;
     StageLayout L;
     int lxh, ly, lz, lt, rows, tile, ntiles, out_parity, reverse;
+    int tpt;     // teams per tile (32 sites each): 1 or 2
+    int groups;  // teams / tpt: tiles computed at once
     long long vh;
     float a;
     float2 *out;
@@ -66,6 +70,12 @@ struct StagedParams {
 };
 
 int round128(int b) { return (b + 127) & ~127; }
+
+// bytes of `stages` stages plus their mbarriers
+size_t staged_smem(const StageLayout &L, int stages)
+{
+    return (size_t)stages * L.bytes + (2 * stages + kTeams) * sizeof(uint64_t);
+}
 
 bool make_layout(int lxh, int rows, bool axpy, StageLayout &L)
 {
@@ -96,7 +106,7 @@ bool make_layout(int lxh, int rows, bool axpy, StageLayout &L)
     L.x = axpy ? take(96 * T) : 0;
     L.bytes = off;
     L.tx = 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + (axpy ? 96 * T : 0);
-    return kStages * L.bytes + 16 * 8 * kStages <= 227 * 1024;
+    return staged_smem(L, 2) <= kSmemLimit;
 }
 
 // ------------------------------------------------------------ PTX helpers --
@@ -310,25 +320,24 @@ __device__ __forceinline__ void staged_dir(cx<float> (&acc)[12], const float2 *s
         reconstruct<MU, S>(acc[col], acc[3 + col], acc[6 + col], acc[9 + col], w[0][col], w[1][col]);
 }
 
-template <bool Dag, bool Axpy>
+template <bool Dag, bool Axpy, int NS>
 __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __grid_constant__ StagedParams P)
 {
     extern __shared__ __align__(128) char smem[];
     const StageLayout &L = P.L;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * L.bytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *ready = empty + kStages;  // [stage][half]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NS * L.bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *ready = empty + NS;  // per team: z/t partial sums written
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const int ntile_cta =
         P.ntiles > (int)blockIdx.x ? (P.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(empty + s, 2);
-            mbar_init(ready + 2 * s, 1);
-            mbar_init(ready + 2 * s + 1, 1);
+            mbar_init(empty + s, (unsigned)P.tpt);  // the x/y warps of the tile's teams
         }
+        for (int t = 0; t < kTeams; ++t) mbar_init(ready + t, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
         const uint64_t pol = policy_evict_first();
         int issued = 0;
         for (int k = 0; k < ntile_cta; ++k) {
-            const int s = k % kStages, n = k / kStages;
+            const int s = k % NS, n = k / NS;
             if (n >= 1 && !mbar_wait(empty + s, (unsigned)((n - 1) & 1), P)) break;
             if (P.inject && k == 0) continue;  // nothing loaded, nothing in flight
             issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + s * L.bytes,
@@ -346,26 +355,29 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
             issued = k + 1;
         }
         // the last loads of each stage must have landed before the CTA exits
-        for (int k = issued - 1; k >= 0 && k >= issued - kStages; --k) {
+        for (int k = issued - 1; k >= 0 && k >= issued - NS; --k) {
             if (P.inject && k == 0) continue;
-            mbar_wait(full + k % kStages, (unsigned)((k / kStages) & 1), P);
+            mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
         }
         return;
     }
 
-    // consumers: group g owns stage g and the CTA's tiles k = g, g + 3, ...
-    const int g = warp >> 2, q = (warp >> 1) & 1, half = warp & 1;
-    const int s = half * 32 + lane;  // site within the tile
+    // consumers: team = two warps (x/y and z/t) on 32 sites of a tile; group g
+    // = tpt teams on one tile, taking the CTA's tiles k = g, g + groups, ...
+    const int team = warp >> 1, q = warp & 1;
+    const int g = team / P.tpt;
+    const int s = (team - g * P.tpt) * 32 + lane;  // site within the tile
     const bool active = s < P.tile;
     const int lxh = P.lxh, T = P.tile;
     const int r = s / lxh, xh = s - r * lxh;
     constexpr int S0 = Dag ? -1 : 1;
-    char *base = smem + g * L.bytes;
-    const float2 *sp0 = reinterpret_cast<const float2 *>(base + L.sp[0]);
-    float2 *part = reinterpret_cast<float2 *>(base + L.sp[3]);  // z/t partial sums
-    for (int k = g; k < ntile_cta; k += kStages) {
-        const unsigned par_n = (unsigned)((k / kStages) & 1);
-        if (!mbar_wait(full + g, par_n, P)) return;
+    unsigned m = 0;  // tiles this team has done
+    for (int k = g; k < ntile_cta; k += P.groups, ++m) {
+        const int st = k % NS;
+        if (!mbar_wait(full + st, (unsigned)((k / NS) & 1), P)) return;
+        char *base = smem + st * L.bytes;
+        const float2 *sp0 = reinterpret_cast<const float2 *>(base + L.sp[0]);
+        float2 *part = reinterpret_cast<float2 *>(base + L.sp[3]);  // z/t partial sums
         const TileGeo tg = tile_geo(P, (int)blockIdx.x + k * (int)gridDim.x);
         cx<float> acc[12];
 #pragma unroll
@@ -402,7 +414,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
                                              lxh, xh, reinterpret_cast<const float4 *>(base + L.ya4),
                                              reinterpret_cast<const float2 *>(base + L.ya2), lxh, xh);
             }
-            if (!mbar_wait(ready + 2 * g + half, par_n, P)) return;
+            if (!mbar_wait(ready + team, m & 1u, P)) return;
             if (active) {
 #pragma unroll
                 for (int c = 0; c < 12; ++c) {
@@ -424,7 +436,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty + g);
+            if (lane == 0) mbar_arrive(empty + st);
         } else {
             if (active) {
                 staged_dir<2, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[3]), T, s,
@@ -446,7 +458,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
             // the next TMA load into this stage writes over the partial sums
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(ready + 2 * g + half);
+            if (lane == 0) mbar_arrive(ready + team);
         }
     }
 }
@@ -484,59 +496,89 @@ bool encode(CUtensorMap *m, const void *ptr, int rank, const cuuint64_t *dims,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// rows of R per tile: the largest R dividing Ly with R * Lx/2 <= 64, R >= 2
-int staged_rows(int lxh, int ly)
+// rows of R per tile: R divides Ly, R >= 2, R * Lx/2 <= 64; the largest such
+// R, or the requested one when it qualifies (0 if none does)
+int staged_rows(int lxh, int ly, int want = 0)
 {
     if (lxh % 2 != 0) return 0;  // rows must start on 16-byte boundaries
+    auto ok = [&](int r) { return r >= 2 && ly % r == 0 && r * lxh <= kMaxTile; };
+    if (want) return ok(want) ? want : 0;
     for (int r = kMaxTile / lxh; r >= 2; --r)
-        if (ly % r == 0) return r;
+        if (ok(r)) return r;
     return 0;
 }
 
-template <bool Dag, bool Axpy>
+// ring depth: the requested one if it fits, else the most that fit (<= 3)
+int staged_depth(const StageLayout &L, int want)
+{
+    if (want) return want >= 2 && want <= kMaxStages && staged_smem(L, want) <= kSmemLimit ? want : 0;
+    for (int d = 3; d >= 2; --d)
+        if (staged_smem(L, d) <= kSmemLimit) return d;
+    return 0;
+}
+
+template <bool Dag, bool Axpy, int NS>
 int launch_staged(const StagedParams &P, int grid, cudaStream_t s)
 {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(hop_staged_kernel<Dag, Axpy>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr = cudaFuncSetAttribute(hop_staged_kernel<Dag, Axpy, NS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     });
     WEO_CUDA(attr);
-    const size_t bytes = (size_t)kStages * P.L.bytes + 4 * kStages * sizeof(uint64_t);
-    hop_staged_kernel<Dag, Axpy><<<grid, kStagedThreads, bytes, s>>>(P);
+    hop_staged_kernel<Dag, Axpy, NS><<<grid, kStagedThreads, staged_smem(P.L, NS), s>>>(P);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
 
+template <int NS>
+int launch_depth(bool dag, bool axpy, const StagedParams &P, int grid, cudaStream_t s)
+{
+    if (dag) return axpy ? launch_staged<true, true, NS>(P, grid, s) : launch_staged<true, false, NS>(P, grid, s);
+    return axpy ? launch_staged<false, true, NS>(P, grid, s) : launch_staged<false, false, NS>(P, grid, s);
+}
+
 }  // namespace
 
-bool staged_eligible(const wilson_eo_s *h)
+// tile rows and ring depth a handle's staged hops use (0, 0 if not eligible)
+void staged_shape(const wilson_eo_s *h, int *rows_out, int *depth_out)
 {
     const int lxh = h->dims[0] / 2;
     StageLayout L;
-    const int rows = staged_rows(lxh, h->dims[1]);
+    int rows = staged_rows(lxh, h->dims[1], h->staged_rows), depth = 0;
     // TMA coordinates are 32-bit: 4 floats per site in the link boxes
-    return rows >= 2 && make_layout(lxh, rows, true, L) && 4 * h->vh < (1ll << 31) &&
-           encoder() != nullptr;
+    if (rows >= 2 && make_layout(lxh, rows, true, L) && 4 * h->vh < (1ll << 31))
+        depth = staged_depth(L, h->staged_depth);
+    if (!depth) rows = 0;
+    *rows_out = rows;
+    *depth_out = depth;
+}
+
+bool staged_eligible(const wilson_eo_s *h)
+{
+    int rows, depth;
+    staged_shape(h, &rows, &depth);
+    return depth > 0 && encoder() != nullptr;
 }
 
 bool staged_arrays_ok(const HopParams &p, bool axpy)
 {
     auto aligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    return aligned(p.in) && aligned(p.gauge) && (!axpy || aligned(p.x)) && (p.gauge_pb & 15) == 0 &&
-           staged_rows(p.lxh, p.ly) >= 2 && 4ll * p.vh < (1ll << 31);
+    return aligned(p.in) && aligned(p.gauge) && (!axpy || aligned(p.x)) && (p.gauge_pb & 15) == 0;
 }
 
 int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
                       bool inject)
 {
-    const int lxh = p.lxh, rows = staged_rows(lxh, p.ly);
-    if (!staged_arrays_ok(p, axpy) || !h->fused_ctrl.ptr)
+    const int lxh = p.lxh;
+    int rows, depth;
+    staged_shape(h, &rows, &depth);
+    if (!depth || !staged_arrays_ok(p, axpy) || !h->fused_ctrl.ptr)
         return set_error(WEO_ERR_UNSUPPORTED, "staged hop: lattice or array alignment not eligible");
     StagedParams P;
     std::memset(&P, 0, sizeof(P));
-    if (!make_layout(lxh, rows, axpy, P.L)) return set_error(WEO_ERR_UNSUPPORTED, "staged hop: tile too large");
+    make_layout(lxh, rows, axpy, P.L);
     const long long vh = p.vh;
     const int T = rows * lxh;
     // spinor: 12 planes of 2 vh floats
@@ -567,6 +609,8 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     P.lt = p.lt;
     P.rows = rows;
     P.tile = T;
+    P.tpt = T > 32 ? 2 : 1;
+    P.groups = kTeams / P.tpt;
     P.ntiles = (int)(vh / T);
     P.out_parity = p.out_parity;
     P.reverse = p.reverse;
@@ -579,8 +623,12 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     int sms = 0;
     WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int grid = P.ntiles < sms ? P.ntiles : sms;
-    if (dag) return axpy ? launch_staged<true, true>(P, grid, s) : launch_staged<true, false>(P, grid, s);
-    return axpy ? launch_staged<false, true>(P, grid, s) : launch_staged<false, false>(P, grid, s);
+    switch (depth) {
+    case 2: return launch_depth<2>(dag, axpy, P, grid, s);
+    case 3: return launch_depth<3>(dag, axpy, P, grid, s);
+    case 4: return launch_depth<4>(dag, axpy, P, grid, s);
+    default: return launch_depth<5>(dag, axpy, P, grid, s);
+    }
 }
 
 }  // namespace weo

@@ -106,6 +106,8 @@ struct wilson_eo_s {
     int alternate = 1;       // second hop walks the sites in reverse order
     int fused_lookahead = 4;     // t-slices the fused kernel's first hop runs ahead
     int fused_threads = 128;
+    int staged_rows = 0;     // staged hop: lattice rows per tile (0: automatic)
+    int staged_depth = 0;    // staged hop: shared-memory stages (0: automatic)
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
     weo::Buffer halo;        // face buffers of the domain-decomposed hop
 };
@@ -141,6 +143,7 @@ std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axp
 // hop_staged.cu: the hopping kernel fed by TMA boxes through a ring of
 // shared-memory stages (FP32 spinors, 18-real FP32 links, one right-hand side)
 bool staged_eligible(const wilson_eo_s *h);
+void staged_shape(const wilson_eo_s *h, int *rows, int *depth);
 bool staged_arrays_ok(const HopParams &p, bool axpy);
 int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
                       bool inject = false);

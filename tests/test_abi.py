@@ -119,6 +119,6 @@ def test_ff_and_residual_mode_reject_null(lib):
 
 
 def test_staging_rejects_null_and_bad_values(lib):
-    assert lib.wilson_eo_set_staging(None, 1) == -1
-    assert lib.wilson_eo_get_staging(None, None) == -1
+    assert lib.wilson_eo_set_staging(None, 1, 0, 0) == -1
+    assert lib.wilson_eo_get_staging(None, None, None, None) == -1
     assert lib.wilson_eo_inject_staged_timeout(None, None, None, None) == -1

@@ -34,7 +34,7 @@ def test_staged_hop_matches_oracle(weo, oracle_lib, dims):
     x = to_device(to_planar(psi), "f32")
     ref = {(par, dag): op.hop(x, par, dag=dag) for par in (0, 1) for dag in (False, True)}
     weo.wilson_eo_set_staging(op.handle, True)
-    assert weo.wilson_eo_get_staging(op.handle)
+    assert weo.wilson_eo_get_staging(op.handle)["staged"]
     for par in (0, 1):
         for dag in (False, True):
             y = op.hop(x, par, dag=dag)
@@ -124,7 +124,7 @@ def test_staged_rejects_ineligible_lattices(weo, dims, prec, fmt):
         with pytest.raises(weo.WilsonEOError) as e:
             weo.wilson_eo_set_staging(op.handle, True)
         assert e.value.status == -3
-        assert not weo.wilson_eo_get_staging(op.handle)
+        assert weo.wilson_eo_get_staging(op.handle) == {"staged": False, "rows": 0, "depth": 0}
     else:
         weo.wilson_eo_set_staging(op.handle, True)
     op.close()
@@ -170,4 +170,37 @@ def test_staged_bounded_wait_reports_timeout_and_recovers(weo, oracle_lib):
     y = op.hop(x, 1)
     weo.wilson_eo_check(op.handle)
     assert rel_l2(from_planar(y.cpu().numpy()), oracle_lib.hop(U, psi, dims, 1)) <= TOL["f32"]
+    op.close()
+
+
+@pytest.mark.parametrize("rows,depth", [(2, 2), (2, 3), (2, 5), (4, 2), (4, 4), (8, 2), (8, 3)])
+def test_staged_tile_and_ring_shapes(weo, oracle_lib, rows, depth):
+    """16^4: tiles of 16, 32 and 64 sites (one or two teams per tile, six or
+    three tiles computed at once) with rings of 2 to 5 stages."""
+    dims = (16, 16, 16, 16)
+    U = gen.gauge_field(dims, "smooth", seed=310, eps=0.4)
+    psi = gen.gaussian_spinor(dims, seed=311)[0]
+    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
+    weo.wilson_eo_set_staging(op.handle, True, rows, depth)
+    assert weo.wilson_eo_get_staging(op.handle) == {"staged": True, "rows": rows, "depth": depth}
+    x = to_device(to_planar(psi), "f32")
+    for dag in (False, True):
+        y = op.apply(x, dag=dag)
+        weo.wilson_eo_check(op.handle)
+        f = oracle_lib.meo_dag if dag else oracle_lib.meo
+        assert rel_l2(from_planar(y.cpu().numpy()), f(U, 0.13, psi, dims)) <= TOL["f32"]
+    op.close()
+
+
+def test_staged_rejects_shapes_that_do_not_fit(weo):
+    dims = (32, 8, 4, 4)
+    op = weo.WilsonEO(dims, 0.1, to_device(gen.gauge_field(dims, "haar", seed=2)), prec="f32")
+    for rows, depth in ((4, 4), (3, 0), (16, 0)):  # 4 x 77 KB; 3 does not divide 8; 256 sites
+        with pytest.raises(weo.WilsonEOError) as e:
+            weo.wilson_eo_set_staging(op.handle, True, rows, depth)
+        assert e.value.status == -3
+    with pytest.raises(weo.WilsonEOError) as e:
+        weo.wilson_eo_set_staging(op.handle, True, 0, 6)
+    assert e.value.status == -1
+    assert weo.wilson_eo_get_staging(op.handle) == {"staged": False, "rows": 4, "depth": 3}
     op.close()

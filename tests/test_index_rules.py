@@ -121,11 +121,14 @@ def test_float_float_projector_table(oracle_lib, mu, S):
 # the kernel's tile, box and in-tile index arithmetic and checks that every
 # value it reads is the neighbour spinor / link the hopping sum needs.
 
-def staged_rows(lxh, ly):
+def staged_rows(lxh, ly, want=0):
     if lxh % 2:
         return 0
+    ok = lambda r: r >= 2 and ly % r == 0 and r * lxh <= 64  # noqa: E731
+    if want:
+        return want if ok(want) else 0
     for r in range(64 // lxh, 1, -1):
-        if ly % r == 0:
+        if ok(r):
             return r
     return 0
 
@@ -180,10 +183,11 @@ def staged_reads(dims, rows, geo, s, out_parity):
                                   (48, 4, 2, 2)])
 @pytest.mark.parametrize("out_parity", [0, 1])
 @pytest.mark.parametrize("reverse", [False, True])
-def test_staged_tile_reads(dims, out_parity, reverse):
+@pytest.mark.parametrize("want_rows", [0, 2])
+def test_staged_tile_reads(dims, out_parity, reverse, want_rows):
     lx, ly, lz, lt = dims
     lxh, vh = lx // 2, lx * ly * lz * lt // 2
-    rows = staged_rows(lxh, ly)
+    rows = staged_rows(lxh, ly, want_rows)
     assert rows >= 2 and ly % rows == 0
     T = rows * lxh
     assert T <= 64 and vh % T == 0
@@ -215,24 +219,26 @@ def test_staged_tile_reads(dims, out_parity, reverse):
 
 
 def test_staged_layout_and_byte_count():
-    """Stage regions are 128-byte aligned and disjoint, three stages fit in
-    227 KB for every tile shape the row rule allows, and the mbarrier's expected
-    byte count equals the bytes of the boxes issued."""
-    for lxh in range(2, 33, 2):
-        for ly in range(2, 130, 2):
-            rows = staged_rows(lxh, ly)
-            if rows < 2:
-                continue
-            T = rows * lxh
-            sizes = ([96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [64 * T, 8 * T] * 7 +
-                     [64 * lxh, 8 * lxh, 64 * (rows - 1) * lxh, 8 * (rows - 1) * lxh, 96 * T])
-            off, regions = 0, []
-            for b in sizes:
-                regions.append((off, off + b))
-                off += (b + 127) // 128 * 128
-            assert all(a % 128 == 0 for a, _ in regions)
-            assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
-            fits = 3 * off + 16 * 8 * 3 <= 227 * 1024  # else the plain kernel runs
-            if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)):
-                assert fits, (lxh, ly)
-            assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + 96 * T
+    """Stage regions are 128-byte aligned and disjoint, the ring fits in
+    227 KB for the workload shapes, and the mbarrier's expected byte count
+    equals the bytes of the boxes issued, for every tile shape the row rule
+    allows."""
+    for lxh, ly, want in itertools.product(range(2, 33, 2), range(2, 130, 2), (0, 2, 4)):
+        rows = staged_rows(lxh, ly, want)
+        if rows < 2:
+            continue
+        T = rows * lxh
+        sizes = ([96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [64 * T, 8 * T] * 7 +
+                 [64 * lxh, 8 * lxh, 64 * (rows - 1) * lxh, 8 * (rows - 1) * lxh, 96 * T])
+        off, regions = 0, []
+        for b in sizes:
+            regions.append((off, off + b))
+            off += (b + 127) // 128 * 128
+        assert all(a % 128 == 0 for a, _ in regions)
+        assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
+        ring = {d: d * off + (2 * d + 6) * 8 for d in (2, 3, 4, 5)}
+        if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)) and want == 0:
+            assert ring[3] <= 227 * 1024, (lxh, ly)
+        if (lxh, ly, want) == (16, 32, 2):
+            assert ring[5] <= 227 * 1024
+        assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + 96 * T
