@@ -288,8 +288,8 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
  * sites are cut into tiles of R lattice rows; one producer warp per CTA loads
  * each tile's neighbour-spinor rows (same plane, y-1 / y+R rows, planes z+-1
  * and t+-1), its eight link rows and the axpy addend as cp.async.bulk.tensor
- * boxes into a three-stage shared-memory ring, and twelve consumer warps compute
- * from shared memory. Same arithmetic per direction as the default kernel; the
+ * boxes into a ring of shared-memory stages, and consumer warps compute from
+ * shared memory. Same arithmetic per direction as the default kernel; the
  * x/y and z/t halves of the sum are added at the end, so results agree to
  * FP32 rounding, not bitwise. Needs Lx/2 even and some R >= 2 dividing Ly with
  * R * Lx/2 <= 64 (WEO_ERR_UNSUPPORTED otherwise); arrays whose addresses are
@@ -297,9 +297,10 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
  * (about a second); a wait that gives up is reported by wilson_eo_check as
  * WEO_ERR_TIMEOUT. staged = 0 (default) restores the default kernel.
  * rows: lattice rows R per tile (0: the largest that qualifies); depth: stages
- * of the ring, 2..5 (0: the most up to 3 that fit in 227 KB of shared memory).
- * A tile of R Lx/2 sites is computed by one or two teams of two warps (x/y and
- * z/t directions, 32 sites each); six teams share the CTA. */
+ * of the ring, 2..5 (0: the most up to 3 that fit). A tile of R Lx/2 sites is
+ * computed by one or two teams of two warps (x/y and z/t directions, 32 sites
+ * each); each stage has its own teams, at most six per CTA, and all stages
+ * must fit in 227 KB of shared memory (WEO_ERR_UNSUPPORTED otherwise). */
 int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth);
 
 /* Whether staging is on, and the tile rows and ring depth the handle's lattice

@@ -13,12 +13,13 @@
 //     z-1 and t-1, and for mu = y at row y0-1 (periodic) and rows y0..y0+R-2;
 //   the axpy addend at the tile.
 // One producer warp issues them as cp.async.bulk.tensor loads into a ring of
-// three stages, each with an mbarrier that counts the bytes landed; twelve
-// consumer warps in three groups (one per stage) compute from shared memory
-// only, so the bytes in flight no longer depend on the registers each
-// thread holds. In a group, two warps take the x and y directions and two the
-// z and t directions of 2 x 32 sites; the z/t partial sums are handed over in
-// shared memory (in the slots of the z+1 spinor rows they no longer need).
+// two to five stages, each with an mbarrier that counts the bytes landed. Each
+// stage is owned by one group of consumer teams, which compute from shared
+// memory only, so the bytes in flight no longer depend on the registers each
+// thread holds. A team is two warps on 32 sites of the tile: one takes the x
+// and y directions, the other the z and t directions, whose partial sums are
+// handed over in shared memory (in the slots of the z+1 spinor rows they no
+// longer need); a tile of more than 32 sites has two teams.
 //
 // Every wait is bounded (a time limit on the global timer): on expiry the
 // kernel records an error word that wilson_eo_check reports, stops, and the
@@ -35,7 +36,7 @@ namespace weo {
 
 namespace {
 
-constexpr int kTeams = 6;                        // consumer teams of two warps
+constexpr int kTeams = 6;                        // at most six consumer teams of two warps
 constexpr int kConsumerWarps = 2 * kTeams;
 constexpr int kStagedThreads = 32 * (kConsumerWarps + 1);
 constexpr int kMaxTile = 64;                       // sites per tile (box limits)
@@ -60,7 +61,6 @@ struct StagedParams {
     StageLayout L;
     int lxh, ly, lz, lt, rows, tile, ntiles, out_parity, reverse;
     int tpt;     // teams per tile (32 sites each): 1 or 2
-    int groups;  // teams / tpt: tiles computed at once
     long long vh;
     float a;
     float2 *out;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     }
     __syncthreads();
 
-    if (warp == kConsumerWarps) {  // producer
+    if (warp == 2 * NS * P.tpt) {  // producer
         if (lane != 0) return;
         const uint64_t pol = policy_evict_first();
         int issued = 0;
@@ -363,7 +363,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     }
 
     // consumers: team = two warps (x/y and z/t) on 32 sites of a tile; group g
-    // = tpt teams on one tile, taking the CTA's tiles k = g, g + groups, ...
+    // = tpt teams owning stage g and the CTA's tiles k = g, g + NS, ... Each
+    // barrier's waiter thus always waits for the phase after the one it saw last.
     const int team = warp >> 1, q = warp & 1;
     const int g = team / P.tpt;
     const int s = (team - g * P.tpt) * 32 + lane;  // site within the tile
@@ -371,11 +372,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     const int lxh = P.lxh, T = P.tile;
     const int r = s / lxh, xh = s - r * lxh;
     constexpr int S0 = Dag ? -1 : 1;
-    unsigned m = 0;  // tiles this team has done
-    for (int k = g; k < ntile_cta; k += P.groups, ++m) {
-        const int st = k % NS;
-        if (!mbar_wait(full + st, (unsigned)((k / NS) & 1), P)) return;
-        char *base = smem + st * L.bytes;
+    const int st = g;
+    char *base = smem + st * L.bytes;
+    for (int k = g; k < ntile_cta; k += NS) {
+        const unsigned m = (unsigned)(k / NS);  // use of this stage
+        if (!mbar_wait(full + st, m & 1u, P)) return;
         const float2 *sp0 = reinterpret_cast<const float2 *>(base + L.sp[0]);
         float2 *part = reinterpret_cast<float2 *>(base + L.sp[3]);  // z/t partial sums
         const TileGeo tg = tile_geo(P, (int)blockIdx.x + k * (int)gridDim.x);
@@ -508,12 +509,18 @@ int staged_rows(int lxh, int ly, int want = 0)
     return 0;
 }
 
-// ring depth: the requested one if it fits, else the most that fit (<= 3)
-int staged_depth(const StageLayout &L, int want)
+// ring depth (= tiles computed at once, one group of teams per stage): the
+// requested one if it fits in shared memory and in six teams, else the most
+// that fit (at most 3)
+int staged_depth(const StageLayout &L, int tile, int want)
 {
-    if (want) return want >= 2 && want <= kMaxStages && staged_smem(L, want) <= kSmemLimit ? want : 0;
+    const int tpt = tile > 32 ? 2 : 1;
+    auto ok = [&](int d) {
+        return d >= 2 && d <= kMaxStages && d * tpt <= kTeams && staged_smem(L, d) <= kSmemLimit;
+    };
+    if (want) return ok(want) ? want : 0;
     for (int d = 3; d >= 2; --d)
-        if (staged_smem(L, d) <= kSmemLimit) return d;
+        if (ok(d)) return d;
     return 0;
 }
 
@@ -527,7 +534,8 @@ int launch_staged(const StagedParams &P, int grid, cudaStream_t s)
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     });
     WEO_CUDA(attr);
-    hop_staged_kernel<Dag, Axpy, NS><<<grid, kStagedThreads, staged_smem(P.L, NS), s>>>(P);
+    const int threads = 32 * (2 * NS * P.tpt + 1);  // NS x tpt teams and the producer
+    hop_staged_kernel<Dag, Axpy, NS><<<grid, threads, staged_smem(P.L, NS), s>>>(P);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
@@ -549,7 +557,7 @@ void staged_shape(const wilson_eo_s *h, int *rows_out, int *depth_out)
     int rows = staged_rows(lxh, h->dims[1], h->staged_rows), depth = 0;
     // TMA coordinates are 32-bit: 4 floats per site in the link boxes
     if (rows >= 2 && make_layout(lxh, rows, true, L) && 4 * h->vh < (1ll << 31))
-        depth = staged_depth(L, h->staged_depth);
+        depth = staged_depth(L, rows * lxh, h->staged_depth);
     if (!depth) rows = 0;
     *rows_out = rows;
     *depth_out = depth;
@@ -610,7 +618,6 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     P.rows = rows;
     P.tile = T;
     P.tpt = T > 32 ? 2 : 1;
-    P.groups = kTeams / P.tpt;
     P.ntiles = (int)(vh / T);
     P.out_parity = p.out_parity;
     P.reverse = p.reverse;
