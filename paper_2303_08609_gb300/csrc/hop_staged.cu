@@ -231,10 +231,12 @@ __device__ __forceinline__ int row_start(const StagedParams &P, int z, int t, in
     return ((t * P.lz + z) * P.ly + y) * P.lxh;
 }
 
-// issue the loads of tile j into the stage at `base`
+// issue the loads of tile j into the stage at `base`: one box per lane of the
+// producer warp (25 boxes, 26 with the addend), after lane 0 has told the
+// stage's mbarrier how many bytes to expect
 template <bool Axpy>
 __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *base, uint64_t *full,
-                                           uint64_t pol)
+                                           uint64_t pol, int lane)
 {
     const TileGeo g = tile_geo(P, j);
     const StageLayout &L = P.L;
@@ -246,33 +248,65 @@ __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *b
     const int i0 = (int)g.i0;
     const int i_ym = row_start(P, g.z, g.t, ym);
     const int i_zm = row_start(P, zm, g.t, g.y0), i_tm = row_start(P, g.z, tm, g.y0);
-    mbar_expect_tx(full, (unsigned)L.tx);
-    // input spinor (parity 1-p); the coordinate is in floats, 2 per complex
-    tma_2d(base + L.sp[0], &P.sp_tile, 2 * i0, 0, full);
-    tma_2d(base + L.sp[1], &P.sp_row, 2 * i_ym, 0, full);
-    tma_2d(base + L.sp[2], &P.sp_row, 2 * row_start(P, g.z, g.t, yp), 0, full);
-    tma_2d(base + L.sp[3], &P.sp_tile, 2 * row_start(P, zp, g.t, g.y0), 0, full);
-    tma_2d(base + L.sp[4], &P.sp_tile, 2 * i_zm, 0, full);
-    tma_2d(base + L.sp[5], &P.sp_tile, 2 * row_start(P, g.z, tp, g.y0), 0, full);
-    tma_2d(base + L.sp[6], &P.sp_tile, 2 * i_tm, 0, full);
-    // links (field 2 mu + parity); read once per launch, so evict first
     const int op = P.out_parity, ip = op ^ 1;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        tma_3d_hint(base + L.lf4[mu], &P.lk4_tile, 4 * i0, 0, 2 * mu + op, full, pol);
-        tma_2d_hint(base + L.lf2[mu], &P.lk2_tile, 2 * i0, 2 * mu + op, full, pol);
+    if (lane == 0) mbar_expect_tx(full, (unsigned)L.tx);
+    __syncwarp();
+    // lane -> box. Spinor coordinates are in floats (2 per complex); link
+    // coordinates name the field 2 mu + parity; links are read once per launch,
+    // so they are loaded with an evict-first hint.
+    const CUtensorMap *map = nullptr;
+    int dst = 0, c0 = 0, c1 = 0, c2 = -1;
+    if (lane < 7) {
+        const int start = lane == 0   ? i0
+                          : lane == 1 ? i_ym
+                          : lane == 2 ? row_start(P, g.z, g.t, yp)
+                          : lane == 3 ? row_start(P, zp, g.t, g.y0)
+                          : lane == 4 ? i_zm
+                          : lane == 5 ? row_start(P, g.z, tp, g.y0)
+                                      : i_tm;
+        map = lane == 1 || lane == 2 ? &P.sp_row : &P.sp_tile;
+        dst = lane == 0 ? L.sp[0] : lane == 1 ? L.sp[1] : lane == 2 ? L.sp[2] : lane == 3 ? L.sp[3]
+            : lane == 4 ? L.sp[4] : lane == 5 ? L.sp[5] : L.sp[6];
+        c0 = 2 * start;
+    } else if (lane < 15) {  // forward links U_mu(x) at the tile
+        const int mu = (lane - 7) >> 1;
+        const bool f4 = ((lane - 7) & 1) == 0;
+        map = f4 ? &P.lk4_tile : &P.lk2_tile;
+        const int o4 = mu == 0 ? L.lf4[0] : mu == 1 ? L.lf4[1] : mu == 2 ? L.lf4[2] : L.lf4[3];
+        const int o2 = mu == 0 ? L.lf2[0] : mu == 1 ? L.lf2[1] : mu == 2 ? L.lf2[2] : L.lf2[3];
+        dst = f4 ? o4 : o2;
+        c0 = (f4 ? 4 : 2) * i0;
+        if (f4) c2 = 2 * mu + op;
+        else c1 = 2 * mu + op;
+    } else if (lane < 25) {  // backward links U_mu(x - mu)
+        const int b = (lane - 15) >> 1;  // x, z, t, y row y0-1, y rows y0..
+        const bool f4 = ((lane - 15) & 1) == 0;
+        const int mu = b == 0 ? 0 : b == 1 ? 2 : b == 2 ? 3 : 1;
+        const int start = b == 1 ? i_zm : b == 2 ? i_tm : b == 3 ? i_ym : i0;
+        if (b < 3) {
+            map = f4 ? &P.lk4_tile : &P.lk2_tile;
+            const int o4 = b == 0 ? L.lb4[0] : b == 1 ? L.lb4[2] : L.lb4[3];
+            const int o2 = b == 0 ? L.lb2[0] : b == 1 ? L.lb2[2] : L.lb2[3];
+            dst = f4 ? o4 : o2;
+        } else if (b == 3) {
+            map = f4 ? &P.lk4_row : &P.lk2_row;
+            dst = f4 ? L.ya4 : L.ya2;
+        } else {
+            map = f4 ? &P.lk4_rest : &P.lk2_rest;
+            dst = f4 ? L.yb4 : L.yb2;
+        }
+        c0 = (f4 ? 4 : 2) * start;
+        if (f4) c2 = 2 * mu + ip;
+        else c1 = 2 * mu + ip;
+    } else if (Axpy && lane == 25) {
+        map = &P.x_tile;
+        dst = L.x;
+        c0 = 2 * i0;
     }
-    tma_3d_hint(base + L.lb4[0], &P.lk4_tile, 4 * i0, 0, ip, full, pol);
-    tma_2d_hint(base + L.lb2[0], &P.lk2_tile, 2 * i0, ip, full, pol);
-    tma_3d_hint(base + L.lb4[2], &P.lk4_tile, 4 * i_zm, 0, 4 + ip, full, pol);
-    tma_2d_hint(base + L.lb2[2], &P.lk2_tile, 2 * i_zm, 4 + ip, full, pol);
-    tma_3d_hint(base + L.lb4[3], &P.lk4_tile, 4 * i_tm, 0, 6 + ip, full, pol);
-    tma_2d_hint(base + L.lb2[3], &P.lk2_tile, 2 * i_tm, 6 + ip, full, pol);
-    tma_3d_hint(base + L.ya4, &P.lk4_row, 4 * i_ym, 0, 2 + ip, full, pol);
-    tma_2d_hint(base + L.ya2, &P.lk2_row, 2 * i_ym, 2 + ip, full, pol);
-    tma_3d_hint(base + L.yb4, &P.lk4_rest, 4 * i0, 0, 2 + ip, full, pol);
-    tma_2d_hint(base + L.yb2, &P.lk2_rest, 2 * i0, 2 + ip, full, pol);
-    if (Axpy) tma_2d(base + L.x, &P.x_tile, 2 * i0, 0, full);
+    if (map == nullptr) return;
+    if (lane < 7 || lane == 25) tma_2d(base + dst, map, c0, 0, full);
+    else if (c2 >= 0) tma_3d_hint(base + dst, map, c0, 0, c2, full, pol);
+    else tma_2d_hint(base + dst, map, c0, c1, full, pol);
 }
 
 // one hopping direction from shared memory: spinor planes of stride `ss`
@@ -342,23 +376,39 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     }
     __syncthreads();
 
-    if (warp == 2 * NS * P.tpt) {  // producer
-        if (lane != 0) return;
+    if (warp == 2 * NS * P.tpt) {  // producer warp
+        if (lane < 9 && (Axpy || lane != 2)) {  // the addend's map is only encoded with axpy
+            const CUtensorMap *m = lane == 0   ? &P.sp_tile
+                                   : lane == 1 ? &P.sp_row
+                                   : lane == 2 ? &P.x_tile
+                                   : lane == 3 ? &P.lk4_tile
+                                   : lane == 4 ? &P.lk4_row
+                                   : lane == 5 ? &P.lk4_rest
+                                   : lane == 6 ? &P.lk2_tile
+                                   : lane == 7 ? &P.lk2_row
+                                               : &P.lk2_rest;
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+        }
         const uint64_t pol = policy_evict_first();
         int issued = 0;
         for (int k = 0; k < ntile_cta; ++k) {
             const int s = k % NS, n = k / NS;
-            if (n >= 1 && !mbar_wait(empty + s, (unsigned)((n - 1) & 1), P)) break;
+            if (n >= 1) {
+                int ok = 1;
+                if (lane == 0) ok = mbar_wait(empty + s, (unsigned)((n - 1) & 1), P);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            }
             if (P.inject && k == 0) continue;  // nothing loaded, nothing in flight
             issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + s * L.bytes,
-                             full + s, pol);
+                             full + s, pol, lane);
             issued = k + 1;
         }
         // the last loads of each stage must have landed before the CTA exits
-        for (int k = issued - 1; k >= 0 && k >= issued - NS; --k) {
-            if (P.inject && k == 0) continue;
-            mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
-        }
+        if (lane == 0)
+            for (int k = issued - 1; k >= 0 && k >= issued - NS; --k) {
+                if (P.inject && k == 0) continue;
+                mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
+            }
         return;
     }
 
