@@ -145,7 +145,8 @@ int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, c
                cudaStream_t s)
 {
     const bool staged = h->cfg[prec].staged && prec == WEO_F32 && fmt == WEO_LINK18 &&
-                        io == IO_SAME && p.nrhs == 1 && staged_arrays_ok(p, axpy);
+                        io == IO_SAME && p.nrhs == 1 && staged_arrays_ok(p, axpy) &&
+                        staged_ready(h, p, s);
     int tok = -1;
     if (h->prof) {
         const char *kind = staged ? "hop_staged"
@@ -395,8 +396,17 @@ int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth)
                              "and the requested stages in 227 KB of shared memory");
         }
         DeviceGuard dg(h->device);
-        if (staged) WEO_TRY(fused_prepare(h, 0));  // error word of the bounded waits
         h->cfg[WEO_F32].staged = staged;
+        if (staged) {
+            WEO_TRY(fused_prepare(h, 0));  // error word of the bounded waits
+            if (h->gauge.prec == WEO_F32) {
+                WEO_TRY(staged_prepare(h, h->gauge, 0));
+                WEO_CUDA(cudaStreamSynchronize(0));
+            }
+        } else {
+            h->staged_links.release();
+            h->staged_valid = false;
+        }
         return WEO_OK;
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_set_staging");
@@ -434,6 +444,11 @@ int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e
         p.out = out_o;
         p.out_stride = h->vh * 96;
         if (!staged_arrays_ok(p, false)) return set_error(WEO_ERR_ARG, "arrays must be 16-byte aligned");
+        const bool was = h->cfg[WEO_F32].staged;
+        h->cfg[WEO_F32].staged = 1;
+        const int st = staged_prepare(h, h->gauge, static_cast<cudaStream_t>(stream));
+        h->cfg[WEO_F32].staged = was;
+        WEO_TRY(st);
         return launch_hop_staged(h, false, false, p, static_cast<cudaStream_t>(stream), true);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_staged_timeout");
@@ -499,7 +514,7 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
                         h->gauge_ff.buf.bytes + h->ff_in.bytes + h->ff_out.bytes + h->ff_tmp.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
-                        h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes +
+                        h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes + h->staged_links.bytes +
                         h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
@@ -763,6 +778,7 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->tmp.release();
     h->tmp2.release();
     h->tmp3.release();
+    h->staged_links.release();
     h->even1.release();
     h->stage_in.release();
     h->stage_out.release();

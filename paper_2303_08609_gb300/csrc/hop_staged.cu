@@ -4,22 +4,26 @@
 //
 // The output sites are cut into tiles of R lattice rows: R * Lx/2 consecutive
 // compact indices inside one (z, t) plane. Everything the hopping sum of a tile
-// reads is then a few rectangular boxes of the planar arrays:
+// reads is then a few contiguous blocks:
 //   input spinor (parity 1-p): the tile rows of the same plane (+-x, and +-y
 //     inside the tile), the rows y0-1 and y0+R (periodic in y), and the tile
-//     rows of the planes z+1, z-1, t+1, t-1 (periodic);
-//   links: U_mu(x) at the tile (the four fields of parity p); U_mu(x-mu) of
-//     parity 1-p at the tile rows of the same plane (mu = x), of the planes
-//     z-1 and t-1, and for mu = y at row y0-1 (periodic) and rows y0..y0+R-2;
-//   the axpy addend at the tile.
-// One producer warp issues them as cp.async.bulk.tensor loads into a ring of
-// two to five stages, each with an mbarrier that counts the bytes landed. Each
-// stage is owned by one group of consumer teams, which compute from shared
-// memory only, so the bytes in flight no longer depend on the registers each
-// thread holds. A team is two warps on 32 sites of the tile: one takes the x
-// and y directions, the other the z and t directions, whose partial sums are
-// handed over in shared memory (in the slots of the z+1 spinor rows they no
-// longer need); a tile of more than 32 sites has two teams.
+//     rows of the planes z+1, z-1, t+1, t-1 (periodic): seven boxes of the
+//     planar array, loaded with cp.async.bulk.tensor;
+//   links: the eight links of every output site -- U_mu(x) and U_mu(x-mu)^dag's
+//     source U_mu(x-mu) -- repacked once per gauge field into one block per
+//     tile (direction-major, planar inside), so a tile's links are a single
+//     cp.async.bulk copy. This doubles the links' footprint (each link is
+//     stored for both sites it joins), not their traffic: a hop still reads
+//     each stored link once;
+//   the axpy addend at the tile: one box.
+// One producer thread issues them into a ring of two to five stages, each with
+// an mbarrier that counts the bytes landed. Each stage is owned by one group
+// of consumer teams, which compute from shared memory only, so the bytes in
+// flight no longer depend on the registers each thread holds. A team is two
+// warps on 32 sites of the tile: one takes the x and y directions, the other
+// the z and t directions, whose partial sums are handed over in shared memory
+// (in the slots of the z+1 spinor rows they no longer need); a tile of more
+// than 32 sites has two teams.
 //
 // Every wait is bounded (a time limit on the global timer): on expiry the
 // kernel records an error word that wilson_eo_check reports, stops, and the
@@ -45,19 +49,16 @@ constexpr int kSmemLimit = 227 * 1024;
 
 // shared-memory regions of one stage, byte offsets
 struct StageLayout {
-    int sp[7];      // spinor: tile rows, row y0-1, row y0+R, planes z+1, z-1, t+1, t-1
-    int lf4[4], lf2[4];  // forward links U_mu(x): float4 part, float2 part
-    int lb4[4], lb2[4];  // backward links of x, z, t (index 1 unused)
-    int ya4, ya2, yb4, yb2;  // backward y links: row y0-1, rows y0..y0+R-2
-    int x;          // axpy addend
-    int bytes;      // size of one stage
-    int tx;         // bytes the TMA loads of one tile deliver
+    int sp[7];  // spinor: tile rows, row y0-1, row y0+R, planes z+1, z-1, t+1, t-1
+    int lk;     // the tile's link block: 8 directions x (4 float4 + 1 float2 planes)
+    int x;      // axpy addend
+    int bytes;  // size of one stage
+    int tx;     // bytes the loads of one tile deliver
 };
 
 struct StagedParams {
     CUtensorMap sp_tile, sp_row, x_tile;
-    CUtensorMap lk4_tile, lk4_row, lk4_rest;
-    CUtensorMap lk2_tile, lk2_row, lk2_rest;
+    const char *links;  // link blocks of this output parity, 576 T bytes per tile
     StageLayout L;
     int lxh, ly, lz, lt, rows, tile, ntiles, out_parity, reverse;
     int tpt;     // teams per tile (32 sites each): 1 or 2
@@ -90,22 +91,10 @@ bool make_layout(int lxh, int rows, bool axpy, StageLayout &L)
     L.sp[1] = take(96 * lxh);
     L.sp[2] = take(96 * lxh);
     for (int k = 3; k < 7; ++k) L.sp[k] = take(96 * T);
-    for (int mu = 0; mu < 4; ++mu) {
-        L.lf4[mu] = take(64 * T);
-        L.lf2[mu] = take(8 * T);
-    }
-    L.lb4[1] = L.lb2[1] = 0;
-    for (int mu : {0, 2, 3}) {
-        L.lb4[mu] = take(64 * T);
-        L.lb2[mu] = take(8 * T);
-    }
-    L.ya4 = take(64 * lxh);
-    L.ya2 = take(8 * lxh);
-    L.yb4 = take(64 * (rows - 1) * lxh);
-    L.yb2 = take(8 * (rows - 1) * lxh);
+    L.lk = take(576 * T);
     L.x = axpy ? take(96 * T) : 0;
     L.bytes = off;
-    L.tx = 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + (axpy ? 96 * T : 0);
+    L.tx = 5 * 96 * T + 2 * 96 * lxh + 576 * T + (axpy ? 96 * T : 0);
     return staged_smem(L, 2) <= kSmemLimit;
 }
 
@@ -185,24 +174,13 @@ __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0
         : "memory");
 }
 
-__device__ __forceinline__ void tma_2d_hint(void *dst, const CUtensorMap *map, int c0, int c1,
-                                            uint64_t *bar, uint64_t pol)
+__device__ __forceinline__ void bulk_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
+                                          uint64_t pol)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_3d_hint(void *dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, uint64_t *bar, uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar)),
-        "l"(pol)
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
         : "memory");
 }
 
@@ -231,12 +209,10 @@ __device__ __forceinline__ int row_start(const StagedParams &P, int z, int t, in
     return ((t * P.lz + z) * P.ly + y) * P.lxh;
 }
 
-// issue the loads of tile j into the stage at `base`: one box per lane of the
-// producer warp (25 boxes, 26 with the addend), after lane 0 has told the
-// stage's mbarrier how many bytes to expect
+// issue the loads of tile j into the stage at `base`
 template <bool Axpy>
 __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *base, uint64_t *full,
-                                           uint64_t pol, int lane)
+                                           uint64_t pol)
 {
     const TileGeo g = tile_geo(P, j);
     const StageLayout &L = P.L;
@@ -246,67 +222,19 @@ __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *b
     const int zp = g.z + 1 == lz ? 0 : g.z + 1, zm = g.z == 0 ? lz - 1 : g.z - 1;
     const int tp = g.t + 1 == lt ? 0 : g.t + 1, tm = g.t == 0 ? lt - 1 : g.t - 1;
     const int i0 = (int)g.i0;
-    const int i_ym = row_start(P, g.z, g.t, ym);
-    const int i_zm = row_start(P, zm, g.t, g.y0), i_tm = row_start(P, g.z, tm, g.y0);
-    const int op = P.out_parity, ip = op ^ 1;
-    if (lane == 0) mbar_expect_tx(full, (unsigned)L.tx);
-    __syncwarp();
-    // lane -> box. Spinor coordinates are in floats (2 per complex); link
-    // coordinates name the field 2 mu + parity; links are read once per launch,
-    // so they are loaded with an evict-first hint.
-    const CUtensorMap *map = nullptr;
-    int dst = 0, c0 = 0, c1 = 0, c2 = -1;
-    if (lane < 7) {
-        const int start = lane == 0   ? i0
-                          : lane == 1 ? i_ym
-                          : lane == 2 ? row_start(P, g.z, g.t, yp)
-                          : lane == 3 ? row_start(P, zp, g.t, g.y0)
-                          : lane == 4 ? i_zm
-                          : lane == 5 ? row_start(P, g.z, tp, g.y0)
-                                      : i_tm;
-        map = lane == 1 || lane == 2 ? &P.sp_row : &P.sp_tile;
-        dst = lane == 0 ? L.sp[0] : lane == 1 ? L.sp[1] : lane == 2 ? L.sp[2] : lane == 3 ? L.sp[3]
-            : lane == 4 ? L.sp[4] : lane == 5 ? L.sp[5] : L.sp[6];
-        c0 = 2 * start;
-    } else if (lane < 15) {  // forward links U_mu(x) at the tile
-        const int mu = (lane - 7) >> 1;
-        const bool f4 = ((lane - 7) & 1) == 0;
-        map = f4 ? &P.lk4_tile : &P.lk2_tile;
-        const int o4 = mu == 0 ? L.lf4[0] : mu == 1 ? L.lf4[1] : mu == 2 ? L.lf4[2] : L.lf4[3];
-        const int o2 = mu == 0 ? L.lf2[0] : mu == 1 ? L.lf2[1] : mu == 2 ? L.lf2[2] : L.lf2[3];
-        dst = f4 ? o4 : o2;
-        c0 = (f4 ? 4 : 2) * i0;
-        if (f4) c2 = 2 * mu + op;
-        else c1 = 2 * mu + op;
-    } else if (lane < 25) {  // backward links U_mu(x - mu)
-        const int b = (lane - 15) >> 1;  // x, z, t, y row y0-1, y rows y0..
-        const bool f4 = ((lane - 15) & 1) == 0;
-        const int mu = b == 0 ? 0 : b == 1 ? 2 : b == 2 ? 3 : 1;
-        const int start = b == 1 ? i_zm : b == 2 ? i_tm : b == 3 ? i_ym : i0;
-        if (b < 3) {
-            map = f4 ? &P.lk4_tile : &P.lk2_tile;
-            const int o4 = b == 0 ? L.lb4[0] : b == 1 ? L.lb4[2] : L.lb4[3];
-            const int o2 = b == 0 ? L.lb2[0] : b == 1 ? L.lb2[2] : L.lb2[3];
-            dst = f4 ? o4 : o2;
-        } else if (b == 3) {
-            map = f4 ? &P.lk4_row : &P.lk2_row;
-            dst = f4 ? L.ya4 : L.ya2;
-        } else {
-            map = f4 ? &P.lk4_rest : &P.lk2_rest;
-            dst = f4 ? L.yb4 : L.yb2;
-        }
-        c0 = (f4 ? 4 : 2) * start;
-        if (f4) c2 = 2 * mu + ip;
-        else c1 = 2 * mu + ip;
-    } else if (Axpy && lane == 25) {
-        map = &P.x_tile;
-        dst = L.x;
-        c0 = 2 * i0;
-    }
-    if (map == nullptr) return;
-    if (lane < 7 || lane == 25) tma_2d(base + dst, map, c0, 0, full);
-    else if (c2 >= 0) tma_3d_hint(base + dst, map, c0, 0, c2, full, pol);
-    else tma_2d_hint(base + dst, map, c0, c1, full, pol);
+    const int jt = (int)(g.i0 / P.tile);  // tile index in memory order
+    mbar_expect_tx(full, (unsigned)L.tx);
+    // the links are read once per launch: evict first
+    bulk_hint(base + L.lk, P.links + (long long)jt * 576 * P.tile, (unsigned)(576 * P.tile), full, pol);
+    // input spinor (parity 1-p); the coordinate is in floats, 2 per complex
+    tma_2d(base + L.sp[0], &P.sp_tile, 2 * i0, 0, full);
+    tma_2d(base + L.sp[1], &P.sp_row, 2 * row_start(P, g.z, g.t, ym), 0, full);
+    tma_2d(base + L.sp[2], &P.sp_row, 2 * row_start(P, g.z, g.t, yp), 0, full);
+    tma_2d(base + L.sp[3], &P.sp_tile, 2 * row_start(P, zp, g.t, g.y0), 0, full);
+    tma_2d(base + L.sp[4], &P.sp_tile, 2 * row_start(P, zm, g.t, g.y0), 0, full);
+    tma_2d(base + L.sp[5], &P.sp_tile, 2 * row_start(P, g.z, tp, g.y0), 0, full);
+    tma_2d(base + L.sp[6], &P.sp_tile, 2 * row_start(P, g.z, tm, g.y0), 0, full);
+    if (Axpy) tma_2d(base + L.x, &P.x_tile, 2 * i0, 0, full);
 }
 
 // one hopping direction from shared memory: spinor planes of stride `ss`
@@ -376,39 +304,27 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     }
     __syncthreads();
 
-    if (warp == 2 * NS * P.tpt) {  // producer warp
-        if (lane < 9 && (Axpy || lane != 2)) {  // the addend's map is only encoded with axpy
-            const CUtensorMap *m = lane == 0   ? &P.sp_tile
-                                   : lane == 1 ? &P.sp_row
-                                   : lane == 2 ? &P.x_tile
-                                   : lane == 3 ? &P.lk4_tile
-                                   : lane == 4 ? &P.lk4_row
-                                   : lane == 5 ? &P.lk4_rest
-                                   : lane == 6 ? &P.lk2_tile
-                                   : lane == 7 ? &P.lk2_row
-                                               : &P.lk2_rest;
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
-        }
+    if (warp == 2 * NS * P.tpt) {  // producer
+        if (lane != 0) return;
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.sp_tile)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.sp_row)) : "memory");
+        if (Axpy)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.x_tile)) : "memory");
         const uint64_t pol = policy_evict_first();
         int issued = 0;
         for (int k = 0; k < ntile_cta; ++k) {
             const int s = k % NS, n = k / NS;
-            if (n >= 1) {
-                int ok = 1;
-                if (lane == 0) ok = mbar_wait(empty + s, (unsigned)((n - 1) & 1), P);
-                if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-            }
+            if (n >= 1 && !mbar_wait(empty + s, (unsigned)((n - 1) & 1), P)) break;
             if (P.inject && k == 0) continue;  // nothing loaded, nothing in flight
             issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + s * L.bytes,
-                             full + s, pol, lane);
+                             full + s, pol);
             issued = k + 1;
         }
         // the last loads of each stage must have landed before the CTA exits
-        if (lane == 0)
-            for (int k = issued - 1; k >= 0 && k >= issued - NS; --k) {
-                if (P.inject && k == 0) continue;
-                mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
-            }
+        for (int k = issued - 1; k >= 0 && k >= issued - NS; --k) {
+            if (P.inject && k == 0) continue;
+            mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
+        }
         return;
     }
 
@@ -440,30 +356,22 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
                 const int xp = par ? (xh + 1 == lxh ? 0 : xh + 1) : xh;
                 const int xm = par ? xh : (xh == 0 ? lxh - 1 : xh - 1);
                 const int rb = r * lxh;
-                staged_dir<0, true, S0>(acc, sp0, T, rb + xp,
-                                        reinterpret_cast<const float4 *>(base + L.lf4[0]),
-                                        reinterpret_cast<const float2 *>(base + L.lf2[0]), T, s);
-                staged_dir<0, false, S0>(acc, sp0, T, rb + xm,
-                                         reinterpret_cast<const float4 *>(base + L.lb4[0]),
-                                         reinterpret_cast<const float2 *>(base + L.lb2[0]), T, rb + xm);
+                // direction d = 2 mu + (backward): links at lk + 72 T d, site s
+                const float4 *l4 = reinterpret_cast<const float4 *>(base + L.lk);
+                const float2 *l2 = reinterpret_cast<const float2 *>(base + L.lk + 64 * T);
+                const int ld4 = 18 * T / 4, ld2 = 9 * T;  // one direction, in float4 / float2
+                staged_dir<0, true, S0>(acc, sp0, T, rb + xp, l4, l2, T, s);
+                staged_dir<0, false, S0>(acc, sp0, T, rb + xm, l4 + ld4, l2 + ld2, T, s);
                 if (r + 1 < P.rows)
-                    staged_dir<1, true, S0>(acc, sp0, T, rb + lxh + xh,
-                                            reinterpret_cast<const float4 *>(base + L.lf4[1]),
-                                            reinterpret_cast<const float2 *>(base + L.lf2[1]), T, s);
+                    staged_dir<1, true, S0>(acc, sp0, T, rb + lxh + xh, l4 + 2 * ld4, l2 + 2 * ld2, T, s);
                 else
                     staged_dir<1, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[2]),
-                                            lxh, xh,
-                                            reinterpret_cast<const float4 *>(base + L.lf4[1]),
-                                            reinterpret_cast<const float2 *>(base + L.lf2[1]), T, s);
+                                            lxh, xh, l4 + 2 * ld4, l2 + 2 * ld2, T, s);
                 if (r > 0)
-                    staged_dir<1, false, S0>(acc, sp0, T, rb - lxh + xh,
-                                             reinterpret_cast<const float4 *>(base + L.yb4),
-                                             reinterpret_cast<const float2 *>(base + L.yb2),
-                                             (P.rows - 1) * lxh, rb - lxh + xh);
+                    staged_dir<1, false, S0>(acc, sp0, T, rb - lxh + xh, l4 + 3 * ld4, l2 + 3 * ld2, T, s);
                 else
                     staged_dir<1, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[1]),
-                                             lxh, xh, reinterpret_cast<const float4 *>(base + L.ya4),
-                                             reinterpret_cast<const float2 *>(base + L.ya2), lxh, xh);
+                                             lxh, xh, l4 + 3 * ld4, l2 + 3 * ld2, T, s);
             }
             if (!mbar_wait(ready + team, m & 1u, P)) return;
             if (active) {
@@ -490,18 +398,17 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
             if (lane == 0) mbar_arrive(empty + st);
         } else {
             if (active) {
+                const float4 *l4 = reinterpret_cast<const float4 *>(base + L.lk);
+                const float2 *l2 = reinterpret_cast<const float2 *>(base + L.lk + 64 * T);
+                const int ld4 = 18 * T / 4, ld2 = 9 * T;
                 staged_dir<2, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[3]), T, s,
-                                        reinterpret_cast<const float4 *>(base + L.lf4[2]),
-                                        reinterpret_cast<const float2 *>(base + L.lf2[2]), T, s);
+                                        l4 + 4 * ld4, l2 + 4 * ld2, T, s);
                 staged_dir<2, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[4]), T, s,
-                                         reinterpret_cast<const float4 *>(base + L.lb4[2]),
-                                         reinterpret_cast<const float2 *>(base + L.lb2[2]), T, s);
+                                         l4 + 5 * ld4, l2 + 5 * ld2, T, s);
                 staged_dir<3, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[5]), T, s,
-                                        reinterpret_cast<const float4 *>(base + L.lf4[3]),
-                                        reinterpret_cast<const float2 *>(base + L.lf2[3]), T, s);
+                                        l4 + 6 * ld4, l2 + 6 * ld2, T, s);
                 staged_dir<3, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[6]), T, s,
-                                         reinterpret_cast<const float4 *>(base + L.lb4[3]),
-                                         reinterpret_cast<const float2 *>(base + L.lb2[3]), T, s);
+                                         l4 + 7 * ld4, l2 + 7 * ld2, T, s);
                 // each lane overwrites only the z+1 slots it read itself
 #pragma unroll
                 for (int c = 0; c < 12; ++c) part[c * T + s] = make_float2(acc[c].r, acc[c].i);
@@ -512,6 +419,46 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
             if (lane == 0) mbar_arrive(ready + team);
         }
     }
+}
+
+// ----------------------------------------------------------- link blocks --
+// Link block of output parity p for tile size T: for output site i (tile
+// i / T, site s = i % T), direction d = 2 mu + b holds U_mu(x) (b = 0) or
+// U_mu(x - mu) (b = 1) as 4 float4 planes then 1 float2 plane of T sites:
+// block(i / T) + 72 T d + 16 T k + 16 s, block + 72 T d + 64 T + 8 s.
+__global__ void pack_link_blocks_kernel(const HopParams p, int T, float *out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.vh) return;
+    int rem = (int)i;
+    const int xh = rem % p.lxh;
+    rem /= p.lxh;
+    const int y = rem % p.ly;
+    rem /= p.ly;
+    const int z = rem % p.lz;
+    const int t = rem / p.lz;
+    const int par = (y + z + t + p.out_parity) & 1;
+    const long long sy = p.lxh, sz = (long long)p.lxh * p.ly, st = sz * p.lz;
+    const long long row = i - xh;
+    const long long nb[4] = {row + (par ? xh : (xh == 0 ? p.lxh - 1 : xh - 1)),
+                             i + (y == 0 ? (p.ly - 1) * sy : -sy),
+                             i + (z == 0 ? (p.lz - 1) * sz : -sz),
+                             i + (t == 0 ? (p.lt - 1) * st : -st)};
+    const long long tile = i / T, s = i % T;
+    char *blk = reinterpret_cast<char *>(out) + tile * 576 * T;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int b = 0; b < 2; ++b) {
+            cx<double> U[3][3];
+            const char *f = p.gauge + (2 * mu + (b ? p.out_parity ^ 1 : p.out_parity)) * p.gauge_pb;
+            LkF32_18::load(f, p.vh, b ? nb[mu] : i, U);
+            char *d = blk + 72ll * T * (2 * mu + b);
+            float4 *q4 = reinterpret_cast<float4 *>(d) + s;
+            q4[0] = make_float4(U[0][0].r, U[0][0].i, U[0][1].r, U[0][1].i);
+            q4[T] = make_float4(U[0][2].r, U[0][2].i, U[1][0].r, U[1][0].i);
+            q4[2 * T] = make_float4(U[1][1].r, U[1][1].i, U[1][2].r, U[1][2].i);
+            q4[3 * T] = make_float4(U[2][0].r, U[2][0].i, U[2][1].r, U[2][1].i);
+            reinterpret_cast<float2 *>(d + 64ll * T)[s] = make_float2(U[2][2].r, U[2][2].i);
+        }
 }
 
 // -------------------------------------------------------- tensor maps --
@@ -605,8 +552,8 @@ void staged_shape(const wilson_eo_s *h, int *rows_out, int *depth_out)
     const int lxh = h->dims[0] / 2;
     StageLayout L;
     int rows = staged_rows(lxh, h->dims[1], h->staged_rows), depth = 0;
-    // TMA coordinates are 32-bit: 4 floats per site in the link boxes
-    if (rows >= 2 && make_layout(lxh, rows, true, L) && 4 * h->vh < (1ll << 31))
+    // TMA coordinates are 32-bit: 2 floats per site in the spinor boxes
+    if (rows >= 2 && make_layout(lxh, rows, true, L) && 2 * h->vh < (1ll << 31))
         depth = staged_depth(L, rows * lxh, h->staged_depth);
     if (!depth) rows = 0;
     *rows_out = rows;
@@ -623,7 +570,62 @@ bool staged_eligible(const wilson_eo_s *h)
 bool staged_arrays_ok(const HopParams &p, bool axpy)
 {
     auto aligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    return aligned(p.in) && aligned(p.gauge) && (!axpy || aligned(p.x)) && (p.gauge_pb & 15) == 0;
+    return aligned(p.in) && (!axpy || aligned(p.x));
+}
+
+// Link blocks of both output parities for the FP32 18-real field g, at the
+// handle's tile size (allocates; not while `s` is being captured).
+int staged_prepare(wilson_eo_s *h, const PackedGauge &g, cudaStream_t s)
+{
+    if (!h->cfg[WEO_F32].staged || g.prec != WEO_F32 || g.fmt != WEO_LINK18) return WEO_OK;
+    int rows, depth;
+    staged_shape(h, &rows, &depth);
+    if (!depth) return WEO_OK;
+    const int T = rows * (h->dims[0] / 2);
+    if (h->staged_valid && h->staged_src == g.buf.ptr && h->staged_gen == g.gen && h->staged_tile == T)
+        return WEO_OK;
+    WEO_TRY(h->staged_links.ensure((size_t)2 * 576 * h->vh));
+    HopParams p = geom_params(h);
+    p.gauge = static_cast<const char *>(g.buf.ptr);
+    p.gauge_pb = g.pb;
+    for (int par = 0; par < 2; ++par) {
+        p.out_parity = par;
+        pack_link_blocks_kernel<<<(unsigned)((h->vh + 255) / 256), 256, 0, s>>>(
+            p, T, reinterpret_cast<float *>(static_cast<char *>(h->staged_links.ptr) + par * 576 * h->vh));
+        WEO_CUDA(cudaGetLastError());
+    }
+    h->staged_valid = true;
+    h->staged_src = g.buf.ptr;
+    h->staged_gen = g.gen;
+    h->staged_tile = T;
+    return WEO_OK;
+}
+
+// the link blocks for gauge pointer `gauge`, if current
+static const char *staged_blocks(const wilson_eo_s *h, const char *gauge, int T)
+{
+    const PackedGauge *g = gauge == h->gauge.buf.ptr ? &h->gauge
+                         : gauge == h->gauge_lo.buf.ptr ? &h->gauge_lo
+                                                        : nullptr;
+    if (!g || !h->staged_valid || h->staged_src != g->buf.ptr || h->staged_gen != g->gen ||
+        h->staged_tile != T)
+        return nullptr;
+    return static_cast<const char *>(h->staged_links.ptr);
+}
+
+bool staged_ready(wilson_eo_s *h, const HopParams &p, cudaStream_t s)
+{
+    int rows, depth;
+    staged_shape(h, &rows, &depth);
+    if (!depth) return false;
+    const int T = rows * p.lxh;
+    if (staged_blocks(h, p.gauge, T)) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    const PackedGauge *g = p.gauge == h->gauge.buf.ptr ? &h->gauge
+                         : p.gauge == h->gauge_lo.buf.ptr ? &h->gauge_lo
+                                                          : nullptr;
+    return g && staged_prepare(h, *g, s) == WEO_OK && staged_blocks(h, p.gauge, T) != nullptr;
 }
 
 int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
@@ -632,8 +634,9 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     const int lxh = p.lxh;
     int rows, depth;
     staged_shape(h, &rows, &depth);
-    if (!depth || !staged_arrays_ok(p, axpy) || !h->fused_ctrl.ptr)
-        return set_error(WEO_ERR_UNSUPPORTED, "staged hop: lattice or array alignment not eligible");
+    const char *blocks = depth ? staged_blocks(h, p.gauge, rows * lxh) : nullptr;
+    if (!blocks || !staged_arrays_ok(p, axpy) || !h->fused_ctrl.ptr)
+        return set_error(WEO_ERR_UNSUPPORTED, "staged hop: lattice, link blocks or array alignment not ready");
     StagedParams P;
     std::memset(&P, 0, sizeof(P));
     make_layout(lxh, rows, axpy, P.L);
@@ -643,24 +646,10 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     const cuuint64_t sd[2] = {(cuuint64_t)(2 * vh), 12};
     const cuuint64_t ss[1] = {(cuuint64_t)(8 * vh)};
     const cuuint32_t b_tile[2] = {(cuuint32_t)(2 * T), 12}, b_row[2] = {(cuuint32_t)(2 * lxh), 12};
-    // links, float4 part: [field][4 planes][4 vh floats]; float2 part: [field][2 vh floats]
-    const cuuint64_t ld4[3] = {(cuuint64_t)(4 * vh), 4, 8};
-    const cuuint64_t ls4[2] = {(cuuint64_t)(16 * vh), (cuuint64_t)p.gauge_pb};
-    const cuuint64_t ld2[2] = {(cuuint64_t)(2 * vh), 8};
-    const cuuint64_t ls2[1] = {(cuuint64_t)p.gauge_pb};
-    const cuuint32_t b4t[3] = {(cuuint32_t)(4 * T), 4, 1}, b4r[3] = {(cuuint32_t)(4 * lxh), 4, 1},
-                     b4s[3] = {(cuuint32_t)(4 * (rows - 1) * lxh), 4, 1};
-    const cuuint32_t b2t[2] = {(cuuint32_t)(2 * T), 1}, b2r[2] = {(cuuint32_t)(2 * lxh), 1},
-                     b2s[2] = {(cuuint32_t)(2 * (rows - 1) * lxh), 1};
-    const char *lk2 = p.gauge + 64 * vh;
-    bool ok = encode(&P.sp_tile, p.in, 2, sd, ss, b_tile) && encode(&P.sp_row, p.in, 2, sd, ss, b_row) &&
-              encode(&P.lk4_tile, p.gauge, 3, ld4, ls4, b4t) &&
-              encode(&P.lk4_row, p.gauge, 3, ld4, ls4, b4r) &&
-              encode(&P.lk4_rest, p.gauge, 3, ld4, ls4, b4s) &&
-              encode(&P.lk2_tile, lk2, 2, ld2, ls2, b2t) && encode(&P.lk2_row, lk2, 2, ld2, ls2, b2r) &&
-              encode(&P.lk2_rest, lk2, 2, ld2, ls2, b2s);
+    bool ok = encode(&P.sp_tile, p.in, 2, sd, ss, b_tile) && encode(&P.sp_row, p.in, 2, sd, ss, b_row);
     if (ok && axpy) ok = encode(&P.x_tile, p.x, 2, sd, ss, b_tile);
     if (!ok) return set_error(WEO_ERR_CUDA, "staged hop: tensor map encoding failed");
+    P.links = blocks + (long long)p.out_parity * 576 * vh;
     P.lxh = lxh;
     P.ly = p.ly;
     P.lz = p.lz;

@@ -117,7 +117,10 @@ int pack_gauge(wilson_eo_s *h, PackedGauge &g, int prec, int fmt, const void *ca
     case kPrecFF: st = pack_with<LkFF18>(g, h, canon, is_f64, s); break;
     default: return set_error(WEO_ERR_ARG, "unknown precision");
     }
-    if (st == WEO_OK) g.valid = true;
+    if (st == WEO_OK) {
+        g.valid = true;
+        ++g.gen;
+    }
     return st;
 }
 

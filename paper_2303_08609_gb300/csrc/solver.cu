@@ -716,6 +716,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
         }
     } else {
         WEO_TRY(lo_gauge(h, &glo, s));
+        WEO_TRY(staged_prepare(h, *glo, s));  // before any capture
         WEO_TRY(S->xs.ensure(b32));
         WEO_TRY(S->rs.ensure(b32));
         WEO_TRY(S->p.ensure(b32));

@@ -65,6 +65,7 @@ struct PackedGauge {
     int fmt = -1;
     long long pb = 0;  // bytes of one (mu, parity) field
     bool valid = false;
+    unsigned gen = 0;  // incremented by every pack
 };
 
 // Launch configuration chosen by the tuner (or defaults).
@@ -108,6 +109,11 @@ struct wilson_eo_s {
     int fused_threads = 128;
     int staged_rows = 0;     // staged hop: lattice rows per tile (0: automatic)
     int staged_depth = 0;    // staged hop: shared-memory stages (0: automatic)
+    weo::Buffer staged_links;   // staged hop: per-tile link blocks of both parities
+    const void *staged_src = nullptr;  // ... packed from this field,
+    unsigned staged_gen = 0;           // ... at this pack generation,
+    int staged_tile = 0;               // ... for tiles of this many sites
+    bool staged_valid = false;
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
     weo::Buffer halo;        // face buffers of the domain-decomposed hop
 };
@@ -145,6 +151,11 @@ std::string kernel_label(const char *kind, int prec, int fmt, bool dag, bool axp
 bool staged_eligible(const wilson_eo_s *h);
 void staged_shape(const wilson_eo_s *h, int *rows, int *depth);
 bool staged_arrays_ok(const HopParams &p, bool axpy);
+// link blocks of the staged hop for field g (no-op unless staging is on)
+int staged_prepare(wilson_eo_s *h, const PackedGauge &g, cudaStream_t s);
+// the link blocks for p.gauge are current, or were built now (never while
+// the stream is being captured)
+bool staged_ready(wilson_eo_s *h, const HopParams &p, cudaStream_t s);
 int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
                       bool inject = false);
 

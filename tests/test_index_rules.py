@@ -117,9 +117,11 @@ def test_float_float_projector_table(oracle_lib, mu, S):
 
 # ---------------------------------------------------------------- staged hop --
 # The TMA-staged hopping kernel (csrc/hop_staged.cu) reads every operand of a
-# tile of R rows from boxes it loaded into shared memory. This model follows
-# the kernel's tile, box and in-tile index arithmetic and checks that every
-# value it reads is the neighbour spinor / link the hopping sum needs.
+# tile of R rows from blocks it loaded into shared memory: seven spinor boxes
+# and the tile's link block (packed once per gauge field: direction d = 2 mu + b
+# of site s holds U_mu(x), or U_mu(x - mu) for b = 1). This model follows the
+# kernel's tile, box and in-tile index arithmetic and checks that every value
+# it reads is the neighbour spinor / link the hopping sum needs.
 
 def staged_rows(lxh, ly, want=0):
     if lxh % 2:
@@ -133,8 +135,8 @@ def staged_rows(lxh, ly, want=0):
     return 0
 
 
-def staged_boxes(dims, rows, j, out_parity):
-    """Boxes of tile j: region -> (array, first compact site, sites, field)."""
+def staged_boxes(dims, rows, j):
+    """Spinor boxes of tile j: region -> (first compact site, sites)."""
     lx, ly, lz, lt = dims
     lxh = lx // 2
     row0 = j * rows
@@ -144,25 +146,15 @@ def staged_boxes(dims, rows, j, out_parity):
     def rs(z_, t_, y_):
         return ((t_ * lz + z_) * ly + y_) * lxh
 
-    ym, yp = (y0 - 1) % ly, (y0 + rows) % ly
-    zp, zm, tp, tm = (z + 1) % lz, (z - 1) % lz, (t + 1) % lt, (t - 1) % lt
-    T, i0, ip = rows * lxh, row0 * lxh, out_parity ^ 1
-    b = {"sp0": ("in", i0, T, None), "sp1": ("in", rs(z, t, ym), lxh, None),
-         "sp2": ("in", rs(z, t, yp), lxh, None), "sp3": ("in", rs(zp, t, y0), T, None),
-         "sp4": ("in", rs(zm, t, y0), T, None), "sp5": ("in", rs(z, tp, y0), T, None),
-         "sp6": ("in", rs(z, tm, y0), T, None)}
-    for mu in range(4):
-        b[f"lf{mu}"] = ("link", i0, T, 2 * mu + out_parity)
-    b["lb0"] = ("link", i0, T, ip)
-    b["lb2"] = ("link", rs(zm, t, y0), T, 4 + ip)
-    b["lb3"] = ("link", rs(z, tm, y0), T, 6 + ip)
-    b["ya"] = ("link", rs(z, t, ym), lxh, 2 + ip)
-    b["yb"] = ("link", i0, (rows - 1) * lxh, 2 + ip)
+    T, i0 = rows * lxh, row0 * lxh
+    b = {"sp0": (i0, T), "sp1": (rs(z, t, (y0 - 1) % ly), lxh), "sp2": (rs(z, t, (y0 + rows) % ly), lxh),
+         "sp3": (rs((z + 1) % lz, t, y0), T), "sp4": (rs((z - 1) % lz, t, y0), T),
+         "sp5": (rs(z, (t + 1) % lt, y0), T), "sp6": (rs(z, (t - 1) % lt, y0), T)}
     return b, (y0, z, t, i0)
 
 
 def staged_reads(dims, rows, geo, s, out_parity):
-    """(direction, spinor region, index, link region, index) as the consumers read them."""
+    """(direction, spinor region, index, link direction) as the consumers read them."""
     lxh = dims[0] // 2
     y0, z, t, _ = geo
     r, xh = divmod(s, lxh)
@@ -170,12 +162,32 @@ def staged_reads(dims, rows, geo, s, out_parity):
     xp = (0 if xh + 1 == lxh else xh + 1) if par else xh
     xm = xh if par else (lxh - 1 if xh == 0 else xh - 1)
     rb = r * lxh
-    out = [((0, 1), "sp0", rb + xp, "lf0", s), ((0, -1), "sp0", rb + xm, "lb0", rb + xm)]
-    out.append(((1, 1), "sp0", rb + lxh + xh, "lf1", s) if r + 1 < rows else ((1, 1), "sp2", xh, "lf1", s))
-    out.append(((1, -1), "sp0", rb - lxh + xh, "yb", rb - lxh + xh) if r > 0 else ((1, -1), "sp1", xh, "ya", xh))
-    out += [((2, 1), "sp3", s, "lf2", s), ((2, -1), "sp4", s, "lb2", s),
-            ((3, 1), "sp5", s, "lf3", s), ((3, -1), "sp6", s, "lb3", s)]
+    out = [((0, 1), "sp0", rb + xp, 0), ((0, -1), "sp0", rb + xm, 1)]
+    out.append(((1, 1), "sp0", rb + lxh + xh, 2) if r + 1 < rows else ((1, 1), "sp2", xh, 2))
+    out.append(((1, -1), "sp0", rb - lxh + xh, 3) if r > 0 else ((1, -1), "sp1", xh, 3))
+    out += [((2, 1), "sp3", s, 4), ((2, -1), "sp4", s, 5), ((3, 1), "sp5", s, 6), ((3, -1), "sp6", s, 7)]
     return out
+
+
+def pack_link_blocks(dims, T, out_parity):
+    """(field, compact index) stored at (tile, direction, site), as the packing
+    kernel writes the link blocks."""
+    lx, ly, lz, lt = dims
+    lxh, vh = lx // 2, lx * ly * lz * lt // 2
+    blk = {}
+    for i in range(vh):
+        xh, rem = i % lxh, i // lxh
+        y, rem = rem % ly, rem // ly
+        z, t = rem % lz, rem // lz
+        par = (y + z + t + out_parity) & 1
+        sy, sz, st = lxh, lxh * ly, lxh * ly * lz
+        nb = [i - xh + (xh if par else (lxh - 1 if xh == 0 else xh - 1)),
+              i + ((ly - 1) * sy if y == 0 else -sy), i + ((lz - 1) * sz if z == 0 else -sz),
+              i + ((lt - 1) * st if t == 0 else -st)]
+        for mu in range(4):
+            blk[(i // T, 2 * mu, i % T)] = (2 * mu + out_parity, i)
+            blk[(i // T, 2 * mu + 1, i % T)] = (2 * mu + (out_parity ^ 1), nb[mu])
+    return blk
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 4, 6, 6), (8, 8, 8, 8), (16, 2, 4, 4),
@@ -190,55 +202,54 @@ def test_staged_tile_reads(dims, out_parity, reverse, want_rows):
     rows = staged_rows(lxh, ly, want_rows)
     assert rows >= 2 and ly % rows == 0
     T = rows * lxh
-    assert T <= 64 and vh % T == 0
+    assert T <= 64 and vh % T == 0 and T % 2 == 0
     ntiles = vh // T
+    blocks = pack_link_blocks(dims, T, out_parity)
     seen = np.zeros(vh, dtype=int)
     for jj in range(ntiles):
         j = ntiles - 1 - jj if reverse else jj
-        boxes, geo = staged_boxes(dims, rows, j, out_parity)
-        for arr, start, n, field in boxes.values():
-            # every box lies inside its array (TMA would zero-fill, not wrap) and
+        boxes, geo = staged_boxes(dims, rows, j)
+        jt = geo[3] // T  # the link block the producer copies
+        for start, n in boxes.values():
+            # every box lies inside the array (TMA would zero-fill, not wrap) and
             # its x coordinate (floats) is a multiple of 16 bytes
             assert 0 <= start and start + n <= vh
-            assert (2 * start * 4) % 16 == 0 and (4 * start * 4) % 16 == 0
-            assert 4 * n <= 256 and 2 * n <= 256
+            assert (2 * start * 4) % 16 == 0 and 2 * n <= 256
         for s in range(T):
             i = geo[3] + s
             seen[i] += 1
             nb, _ = kernel_neighbours(dims, out_parity, i)
-            for d, sreg, si, lreg, li in staged_reads(dims, rows, geo, s, out_parity):
-                arr, start, n, _ = boxes[sreg]
+            for d, sreg, si, ld in staged_reads(dims, rows, geo, s, out_parity):
+                start, n = boxes[sreg]
                 assert 0 <= si < n
                 assert start + si == nb[d], (dims, j, s, d)
-                arr, start, n, field = boxes[lreg]
-                assert 0 <= li < n
                 mu, sgn = d
                 want = (2 * mu + out_parity, i) if sgn > 0 else (2 * mu + (out_parity ^ 1), nb[d])
-                assert (field, start + li) == want, (dims, j, s, d)
+                assert blocks[(jt, ld, s)] == want, (dims, j, s, d)
     assert (seen == 1).all()
 
 
 def test_staged_layout_and_byte_count():
     """Stage regions are 128-byte aligned and disjoint, the ring fits in
-    227 KB for the workload shapes, and the mbarrier's expected byte count
-    equals the bytes of the boxes issued, for every tile shape the row rule
-    allows."""
+    227 KB for the workload shapes, the link block's direction planes start on
+    16-byte boundaries, and the mbarrier's expected byte count equals the bytes
+    copied, for every tile shape the row rule allows."""
     for lxh, ly, want in itertools.product(range(2, 33, 2), range(2, 130, 2), (0, 2, 4)):
         rows = staged_rows(lxh, ly, want)
         if rows < 2:
             continue
         T = rows * lxh
-        sizes = ([96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [64 * T, 8 * T] * 7 +
-                 [64 * lxh, 8 * lxh, 64 * (rows - 1) * lxh, 8 * (rows - 1) * lxh, 96 * T])
+        sizes = [96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [576 * T, 96 * T]
         off, regions = 0, []
         for b in sizes:
             regions.append((off, off + b))
             off += (b + 127) // 128 * 128
         assert all(a % 128 == 0 for a, _ in regions)
         assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
+        assert all((72 * T * d) % 16 == 0 and (72 * T * d + 64 * T) % 16 == 0 for d in range(8))
         ring = {d: d * off + (2 * d + 6) * 8 for d in (2, 3, 4, 5)}
         if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)) and want == 0:
             assert ring[3] <= 227 * 1024, (lxh, ly)
         if (lxh, ly, want) == (16, 32, 2):
             assert ring[5] <= 227 * 1024
-        assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 8 * 72 * T + 96 * T
+        assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 576 * T + 96 * T
