@@ -249,7 +249,9 @@ int wilson_eo_apply_batch_rhs(int n, const wilson_eo_t *hs, void *const *outs,
  * algorithm with threads 64/128/192/256 per CTA and 1, 2 or 4 right-hand sides
  * per thread or 2 on neighbouring lanes (FP32 / 16-bit handles, nrhs >= 2), and
  * for FP32 / 16-bit handles the fused algorithm with a lookahead of 4 or 8
- * t-slices and 128 / 256 threads (wilson_eo_get_launch, wilson_eo_get_algorithm). threads_out / rhs_block_out describe the winner. Results
+ * t-slices and 128 / 256 threads, and for FP32 18-real handles with nrhs = 1
+ * the TMA-staged hop (wilson_eo_get_launch, wilson_eo_get_algorithm,
+ * wilson_eo_get_staging). threads_out / rhs_block_out describe the winner. Results
  * are cached per process by (GPU, extents, precision, link format, nrhs) and,
  * if the environment variable WILSON_EO_TUNE_CACHE names a file, appended to it
  * and read back by later processes. Allocates two temporary spinor fields.

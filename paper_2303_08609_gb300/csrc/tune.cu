@@ -25,6 +25,7 @@ namespace weo {
 struct TuneEntry {
     int algo, threads, rhs_block, lanes, lookahead;
     double ms;
+    int staged = 0;  // FP32 18-real hops through the TMA-staged kernel
 };
 
 static std::mutex g_tune_mutex;
@@ -57,11 +58,15 @@ static void load_tune_file()
     if (!path || !*path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char tag[8], key[400];
-    TuneEntry e;
-    while (fscanf(f, "%7s %399s %d %d %d %d %d %lf", tag, key, &e.algo, &e.threads, &e.rhs_block,
-                  &e.lanes, &e.lookahead, &e.ms) == 8)
-        if (strcmp(tag, "v3") == 0) g_tune_cache[key] = e;
+    char line[640], key[400];
+    while (fgets(line, sizeof(line), f)) {
+        TuneEntry e;
+        if (sscanf(line, "v4 %399s %d %d %d %d %d %lf %d", key, &e.algo, &e.threads, &e.rhs_block,
+                   &e.lanes, &e.lookahead, &e.ms, &e.staged) == 8 ||
+            sscanf(line, "v3 %399s %d %d %d %d %d %lf", key, &e.algo, &e.threads, &e.rhs_block,
+                   &e.lanes, &e.lookahead, &e.ms) == 7)
+            g_tune_cache[key] = e;
+    }
     fclose(f);
 }
 
@@ -71,12 +76,12 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "v3 %s %d %d %d %d %d %.6f\n", key.c_str(), e.algo, e.threads, e.rhs_block, e.lanes,
-            e.lookahead, e.ms);
+    fprintf(f, "v4 %s %d %d %d %d %d %.6f %d\n", key.c_str(), e.algo, e.threads, e.rhs_block,
+            e.lanes, e.lookahead, e.ms, e.staged);
     fclose(f);
 }
 
-static void apply_entry(wilson_eo_s *h, const TuneEntry &e)
+static int apply_entry(wilson_eo_s *h, const TuneEntry &e, cudaStream_t s)
 {
     h->algo = e.algo;
     if (e.algo == 1) {
@@ -87,6 +92,14 @@ static void apply_entry(wilson_eo_s *h, const TuneEntry &e)
         h->cfg[h->prec].rhs_block = e.rhs_block;
         h->cfg[h->prec].lanes = e.lanes;
     }
+    if (h->prec == WEO_F32) {
+        h->cfg[WEO_F32].staged = e.staged;
+        if (e.staged) {
+            WEO_TRY(fused_prepare(h, s));
+            WEO_TRY(staged_prepare(h, h->gauge, s));
+        }
+    }
+    return WEO_OK;
 }
 
 int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int *rhs_out,
@@ -99,7 +112,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             const TuneEntry &e = it->second;
-            apply_entry(h, e);
+            WEO_TRY(apply_entry(h, e, s));
             if (threads_out) *threads_out = e.threads;
             if (rhs_out) *rhs_out = e.rhs_block;
             if (ms_out) *ms_out = e.ms;
@@ -128,7 +141,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     const int saved_algo = h->algo, saved_la = h->fused_lookahead, saved_fthreads = h->fused_threads;
     Profiler *saved_prof = h->prof;
     h->prof = nullptr;
-    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30};
+    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30, saved.staged};
     std::vector<TuneEntry> cands;
     for (int threads : {64, 128, 192, 256}) {
         for (int r : rb) cands.push_back({0, threads, r, 1, 0, 0.0});
@@ -137,8 +150,13 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     if (h->prec != WEO_F64)
         for (int la : {4, 8})
             for (int threads : {128, 256}) cands.push_back({1, threads, 1, 1, la, 0.0});
+    if (h->prec == WEO_F32 && h->fmt == WEO_LINK18 && nrhs == 1 && staged_eligible(h))
+        cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
     for (const TuneEntry &c : cands) {
-        apply_entry(h, c);
+        if (apply_entry(h, c, s) != WEO_OK) {
+            (void)cudaGetLastError();
+            continue;
+        }
         bool ok = true;
         for (int w = 0; w < 2 && ok; ++w) ok = meo_device(h, out.ptr, in.ptr, nrhs, false, s) == WEO_OK;
         if (!ok) {
@@ -153,7 +171,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
             (void)cudaGetLastError();
             continue;
         }
-        if (c.algo == 1) {
+        if (c.algo == 1 || c.staged) {
             unsigned int err = 0;
             if (fused_take_error(h, s, &err) != WEO_OK || err) continue;
         }
@@ -175,7 +193,11 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     h->fused_lookahead = saved_la;
     h->fused_threads = saved_fthreads;
     if (best.ms >= 1e30) return set_error(WEO_ERR_CUDA, "no launch configuration ran");
-    apply_entry(h, best);
+    WEO_TRY(apply_entry(h, best, s));
+    if (!h->cfg[WEO_F32].staged) {  // the trial's link blocks are not kept
+        h->staged_links.release();
+        h->staged_valid = false;
+    }
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = best;

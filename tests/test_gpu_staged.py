@@ -204,3 +204,22 @@ def test_staged_rejects_shapes_that_do_not_fit(weo):
     assert e.value.status == -1
     assert weo.wilson_eo_get_staging(op.handle) == {"staged": False, "rows": 4, "depth": 3}
     op.close()
+
+
+def test_tuner_considers_the_staged_hop(weo, oracle_lib):
+    """wilson_eo_tune with one right-hand side times the staged hop beside the
+    other configurations; whichever wins, M_eo stays correct."""
+    dims = (16, 16, 16, 16)
+    U = gen.gauge_field(dims, "smooth", seed=312, eps=0.4)
+    psi = gen.gaussian_spinor(dims, seed=313)[0]
+    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
+    threads, rb, ms = weo.wilson_eo_tune(op.handle, nrhs=1)
+    assert ms > 0
+    st = weo.wilson_eo_get_staging(op.handle)
+    assert st["rows"] == 8 and st["depth"] == 3
+    y = op.apply(to_device(to_planar(psi), "f32"))
+    weo.wilson_eo_check(op.handle)
+    assert rel_l2(from_planar(y.cpu().numpy()), oracle_lib.meo(U, 0.13, psi, dims)) <= TOL["f32"]
+    if not st["staged"]:
+        assert op.info()["device_bytes"] < 60 * 2**20  # the trial's link blocks (36 MiB) were released
+    op.close()
