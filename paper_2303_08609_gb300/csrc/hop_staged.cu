@@ -68,13 +68,6 @@ static const PackedGauge *field_of(const wilson_eo_s *h, const char *gauge)
 // ring depth cap when none is requested (measured best at tiles of 64 sites)
 static int depth_cap(int prec) { return prec == WEO_F32 ? 3 : 4; }
 
-// ring depths compiled for a format (launch_hop_staged and the 16-bit files)
-static bool depth_compiled(int prec, int fmt, int d)
-{
-    if (prec == WEO_F32) return fmt == WEO_LINK12 ? (d == 2 || d == 3) : (d >= 2 && d <= 5);
-    return d == 3 || d == 4;
-}
-
 static bool format_ok(const wilson_eo_s *h, int prec)
 {
     // 16-bit row blocks (52 Lx/2 bytes) must start on 16-byte boundaries
@@ -92,12 +85,9 @@ void staged_shape(const wilson_eo_s *h, int *rows_out, int *depth_out)
     int rows = tile_rows(lxh, h->dims[1], h->staged_rows), depth = 0;
     // TMA coordinates are 32-bit: 2 floats per site in the spinor boxes
     if (rows >= 2 && format_ok(h, prec) && 2 * h->vh < (1ll << 31)) {
-        // the larger of the two hops' stages: FP32 with the addend; for 16-bit
-        // storage the first hop (FP32 in, no addend)
         StageLayout L;
-        make_layout(lxh, rows, 96, (int)link_site_bytes(prec, h->fmt), prec == WEO_F32, L);
+        make_layout(lxh, rows, 96, (int)link_site_bytes(prec, h->fmt), true, L);
         depth = pick_depth(L, rows * lxh, h->staged_depth, depth_cap(prec));
-        if (depth && !depth_compiled(prec, h->fmt, depth)) depth = 0;
     }
     if (!depth) rows = 0;
     *rows_out = rows;
