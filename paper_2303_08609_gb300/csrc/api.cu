@@ -142,18 +142,20 @@ static int upload_gauge(wilson_eo_s *h, const void *gauge, int gauge_is_f64, cud
 }
 
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
-               cudaStream_t s, bool rb16)
+               cudaStream_t s)
 {
-    const bool staged = rb16 || (io == IO_SAME && prec == WEO_F32 && h->cfg[prec].staged &&
-                                 staged_arrays_ok(p, axpy) && staged_ready(h, p, s));
+    const bool staged = h->cfg[prec].staged && prec == WEO_F32 && fmt == WEO_LINK18 &&
+                        io == IO_SAME && p.nrhs == 1 && staged_arrays_ok(p, axpy) &&
+                        staged_ready(h, p, s);
     int tok = -1;
     if (h->prof) {
-        const char *kind = io == IO_TO16   ? (staged ? "hop_staged_to16" : "hop_to16")
-                           : io == IO_FROM16 ? (staged ? "hop_staged_from16" : "hop_from16")
-                                             : (staged ? "hop_staged" : "hop");
+        const char *kind = staged ? "hop_staged"
+                           : io == IO_TO16   ? "hop_to16"
+                           : io == IO_FROM16 ? "hop_from16"
+                                             : "hop";
         tok = prof_begin(h, kernel_label(kind, prec, fmt, dag, axpy).c_str(), s);
     }
-    int st = staged ? launch_hop_staged(h, io, dag, axpy, p, s)
+    int st = staged ? launch_hop_staged(h, dag, axpy, p, s)
                     : launch_hop(prec, fmt, io, dag, axpy, p, h->cfg[prec], s);
     prof_end(h, tok, s);
     return st;
@@ -204,12 +206,7 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
     p.in_stride = ext;
     p.out = tmp.ptr;
     p.out_stride = s16;
-    // staged hops keep the 16-bit intermediate in their row blocks, so both
-    // hops run staged or neither does
-    auto aligned = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    const bool rb16 = h->cfg[prec].staged && aligned(in) && aligned(out) && aligned(tmp.ptr) &&
-                      staged_ready(h, p, s);
-    WEO_TRY(handle_hop(h, prec, g.fmt, IO_TO16, dag, false, p, s, rb16));
+    WEO_TRY(handle_hop(h, prec, g.fmt, IO_TO16, dag, false, p, s));
     p.out_parity = 0;
     p.in = tmp.ptr;
     p.in_stride = s16;
@@ -219,7 +216,7 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
     p.x_stride = ext;
     p.a = -h->kappa * h->kappa;
     p.reverse = h->alternate;
-    return handle_hop(h, prec, g.fmt, IO_FROM16, dag, true, p, s, rb16);
+    return handle_hop(h, prec, g.fmt, IO_FROM16, dag, true, p, s);
 }
 
 int meo_device(wilson_eo_s *h, void *out, const void *in, int nrhs, bool dag, cudaStream_t s)
@@ -381,10 +378,6 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
     return WEO_OK;
 }
 
-// precision of the handle's operator the staged hop applies to (the FP32 inner
-// operator of an FP64 handle's mixed solver)
-static int staged_prec(const wilson_eo_s *h) { return h->prec == WEO_F64 ? WEO_F32 : h->prec; }
-
 int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth)
 {
     try {
@@ -399,16 +392,14 @@ int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth)
             h->staged_rows = old_rows;
             h->staged_depth = old_depth;
             return set_error(WEO_ERR_UNSUPPORTED,
-                             "staged hop: needs Lx/2 even (a multiple of 4 for 16-bit storage) and "
-                             "R >= 2 dividing Ly with R Lx/2 <= 64, and the requested stages in "
-                             "227 KB of shared memory");
+                             "staged hop: needs Lx/2 even and R >= 2 dividing Ly with R Lx/2 <= 64, "
+                             "and the requested stages in 227 KB of shared memory");
         }
         DeviceGuard dg(h->device);
-        const int sp = staged_prec(h);
-        h->cfg[sp].staged = staged;
+        h->cfg[WEO_F32].staged = staged;
         if (staged) {
             WEO_TRY(fused_prepare(h, 0));  // error word of the bounded waits
-            if (h->gauge.prec == sp) {
+            if (h->gauge.prec == WEO_F32) {
                 WEO_TRY(staged_prepare(h, h->gauge, 0));
                 WEO_CUDA(cudaStreamSynchronize(0));
             }
@@ -427,7 +418,7 @@ int wilson_eo_get_staging(wilson_eo_t h, int *staged, int *rows, int *depth)
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
     int r = 0, d = 0;
     staged_shape(h, &r, &d);
-    if (staged) *staged = h->cfg[staged_prec(h)].staged;
+    if (staged) *staged = h->cfg[WEO_F32].staged;
     if (rows) *rows = r;
     if (depth) *depth = d;
     return WEO_OK;
@@ -437,8 +428,8 @@ int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e
 {
     try {
         if (!h || !out_o || !in_e) return set_error(WEO_ERR_ARG, "NULL handle or array");
-        if (h->prec != WEO_F32 || !staged_eligible(h))
-            return set_error(WEO_ERR_UNSUPPORTED, "staged hop: FP32 handle on an eligible lattice");
+        if (h->prec != WEO_F32 || h->fmt != WEO_LINK18 || !staged_eligible(h))
+            return set_error(WEO_ERR_UNSUPPORTED, "staged hop: FP32 18-real handle on an eligible lattice");
         if (!is_device_pointer(out_o) || !is_device_pointer(in_e))
             return set_error(WEO_ERR_ARG, "device arrays only");
         DeviceGuard dg(h->device);
@@ -458,7 +449,7 @@ int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e
         const int st = staged_prepare(h, h->gauge, static_cast<cudaStream_t>(stream));
         h->cfg[WEO_F32].staged = was;
         WEO_TRY(st);
-        return launch_hop_staged(h, IO_SAME, false, false, p, static_cast<cudaStream_t>(stream), true);
+        return launch_hop_staged(h, false, false, p, static_cast<cudaStream_t>(stream), true);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_staged_timeout");
     }

@@ -92,8 +92,8 @@ static int apply_entry(wilson_eo_s *h, const TuneEntry &e, cudaStream_t s)
         h->cfg[h->prec].rhs_block = e.rhs_block;
         h->cfg[h->prec].lanes = e.lanes;
     }
-    if (h->prec != WEO_F64) {
-        h->cfg[h->prec].staged = e.staged;
+    if (h->prec == WEO_F32) {
+        h->cfg[WEO_F32].staged = e.staged;
         if (e.staged) {
             WEO_TRY(fused_prepare(h, s));
             WEO_TRY(staged_prepare(h, h->gauge, s));
@@ -150,7 +150,8 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     if (h->prec != WEO_F64)
         for (int la : {4, 8})
             for (int threads : {128, 256}) cands.push_back({1, threads, 1, 1, la, 0.0});
-    if (h->prec != WEO_F64 && nrhs == 1 && staged_eligible(h)) cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
+    if (h->prec == WEO_F32 && h->fmt == WEO_LINK18 && nrhs == 1 && staged_eligible(h))
+        cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
     for (const TuneEntry &c : cands) {
         if (apply_entry(h, c, s) != WEO_OK) {
             (void)cudaGetLastError();
@@ -193,7 +194,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     h->fused_threads = saved_fthreads;
     if (best.ms >= 1e30) return set_error(WEO_ERR_CUDA, "no launch configuration ran");
     WEO_TRY(apply_entry(h, best, s));
-    if (h->prec == WEO_F64 || !h->cfg[h->prec].staged) {  // the trial's link blocks are not kept
+    if (!h->cfg[WEO_F32].staged) {  // the trial's link blocks are not kept
         h->staged_links.release();
         h->staged_valid = false;
     }

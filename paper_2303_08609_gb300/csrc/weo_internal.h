@@ -156,22 +156,12 @@ int staged_prepare(wilson_eo_s *h, const PackedGauge &g, cudaStream_t s);
 // the link blocks for p.gauge are current, or were built now (never while
 // the stream is being captured)
 bool staged_ready(wilson_eo_s *h, const HopParams &p, cudaStream_t s);
-// io: IO_SAME (FP32 planar in and out), IO_TO16 (FP32 planar in, 16-bit row
-// blocks out), IO_FROM16 (16-bit row blocks in, FP32 planar out, axpy)
-int launch_hop_staged(wilson_eo_s *h, int io, bool dag, bool axpy, const HopParams &p,
-                      cudaStream_t s, bool inject = false);
-int staged_launch_h16(wilson_eo_s *h, int io, bool c12, bool dag, const HopParams &p,
-                      const char *blocks, int rows, int want, int cap, cudaStream_t s, bool inject);
-int staged_launch_b16(wilson_eo_s *h, int io, bool c12, bool dag, const HopParams &p,
-                      const char *blocks, int rows, int want, int cap, cudaStream_t s, bool inject);
-int staged_pack_h16(const HopParams &p, bool c12, int T, char *out, cudaStream_t s);
-int staged_pack_b16(const HopParams &p, bool c12, int T, char *out, cudaStream_t s);
+int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
+                      bool inject = false);
 
-// launch_hop for a handle, with its launch configuration and profiling;
-// rb16: the 16-bit intermediate is in the staged hop's row blocks (both hops
-// of the M_eo run staged)
+// launch_hop for a handle, with its launch configuration and profiling
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
-               cudaStream_t s, bool rb16 = false);
+               cudaStream_t s);
 
 // M_eo / M_eo^dag with a given packed gauge field (its precision decides the
 // spinor formats) and odd-site buffer (api.cu)

@@ -130,67 +130,21 @@ def test_staged_rejects_ineligible_lattices(weo, dims, prec, fmt):
     op.close()
 
 
-@pytest.mark.parametrize("prec,fmt", [("f32", 12), ("f16", 18), ("f16", 12), ("bf16", 18),
-                                      ("bf16", 12)])
-@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (16, 16, 16, 16), (24, 12, 4, 6)])
-def test_staged_other_formats(weo, oracle_lib, prec, fmt, dims):
-    """12-real FP32 links, and FP16 / BF16 storage, where both hops run staged
-    and the 16-bit intermediate lives in the staged kernel's row blocks: M_eo and
-    M_eo^dag against the oracle, and against the default kernels."""
-    U = gen.gauge_field(dims, "smooth", seed=306, eps=0.4)
-    psi = gen.gaussian_spinor(dims, seed=307)[0]
-    op = weo.WilsonEO(dims, 0.125, to_device(U), prec=prec, linkfmt=fmt)
-    x = to_device(to_planar(psi), "f32")
-    ref = {d: op.apply(x, dag=d) for d in (False, True)}
-    weo.wilson_eo_set_staging(op.handle, True)
-    assert weo.wilson_eo_get_staging(op.handle)["staged"]
-    for dag in (False, True):
-        y = op.apply(x, dag=dag)
-        weo.wilson_eo_check(op.handle)
-        f = oracle_lib.meo_dag if dag else oracle_lib.meo
-        assert rel_l2(from_planar(y.cpu().numpy()), f(U, 0.125, psi, dims)) <= TOL[prec]
-        # same storage rounding (per-site norms, 16-bit values) as the default path
-        assert rel_l2(y.cpu().numpy(), ref[dag].cpu().numpy()) <= (1e-6 if prec == "f32" else 1e-5)
-    op.close()
-
-
-def test_staged_multi_rhs_and_16bit_row_rule_keep_the_default_kernel(weo, oracle_lib):
-    """Two right-hand sides, or 16-bit storage with Lx/2 not a multiple of 4
-    (16-bit row blocks would not start on 16-byte boundaries): staging is
-    refused or skipped and the results stay correct."""
+def test_staged_other_formats_keep_the_default_kernel(weo, oracle_lib):
+    """Staging on, but 12-real links / FP16 storage / two right-hand sides: the
+    default kernels run and the results stay correct."""
     dims = (8, 8, 8, 8)
     U = gen.gauge_field(dims, "smooth", seed=306, eps=0.4)
     psi = gen.gaussian_spinor(dims, nrhs=2, seed=307)
-    op = weo.WilsonEO(dims, 0.125, to_device(U), prec="f32")
-    weo.wilson_eo_set_staging(op.handle, True)
-    y = op.apply(to_device(to_planar(psi), "f32"))
-    weo.wilson_eo_check(op.handle)
-    for r in range(2):
-        assert rel_l2(from_planar(y[r].cpu().numpy()), oracle_lib.meo(U, 0.125, psi[r], dims)) <= TOL["f32"]
-    op.close()
-    dims = (12, 4, 4, 4)
-    op = weo.WilsonEO(dims, 0.1, to_device(gen.gauge_field(dims, "haar", seed=3)), prec="f16")
-    with pytest.raises(weo.WilsonEOError) as e:
+    for prec, fmt in (("f32", 12), ("f16", 18), ("f32", 18)):
+        op = weo.WilsonEO(dims, 0.125, to_device(U), prec=prec, linkfmt=fmt)
         weo.wilson_eo_set_staging(op.handle, True)
-    assert e.value.status == -3
-    op.close()
-
-
-def test_staged_16bit_mixed_solve(weo, oracle_lib):
-    """A mixed solve whose FP16 inner operator runs staged (row-block
-    intermediate), to the FP64 oracle's true residual."""
-    dims = (16, 8, 8, 8)
-    U = gen.gauge_field(dims, "smooth", seed=314, eps=0.4)
-    b = gen.gaussian_spinor(dims, seed=315)[0]
-    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f16", linkfmt=12)
-    weo.wilson_eo_set_staging(op.handle, True)
-    xs, info = op.solve(to_device(to_planar(b)), tol=1e-10, mixed=True)
-    weo.wilson_eo_check(op.handle)
-    assert info["converged"]
-    xg = from_planar(xs.cpu().numpy())
-    ax = oracle_lib.meo_dag(U, 0.13, oracle_lib.meo(U, 0.13, xg, dims), dims)
-    assert np.linalg.norm(b - ax) / np.linalg.norm(b) <= 1.5e-10
-    op.close()
+        y = op.apply(to_device(to_planar(psi), "f32"))
+        weo.wilson_eo_check(op.handle)
+        for r in range(2):
+            assert rel_l2(from_planar(y[r].cpu().numpy()),
+                          oracle_lib.meo(U, 0.125, psi[r], dims)) <= TOL[prec]
+        op.close()
 
 
 def test_staged_bounded_wait_reports_timeout_and_recovers(weo, oracle_lib):

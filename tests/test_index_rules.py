@@ -212,14 +212,9 @@ def test_staged_tile_reads(dims, out_parity, reverse, want_rows):
         jt = geo[3] // T  # the link block the producer copies
         for start, n in boxes.values():
             # every box lies inside the array (TMA would zero-fill, not wrap) and
-            # its x coordinate (floats) is a multiple of 16 bytes; 16-bit row
-            # blocks (52 Lx/2 bytes per row) are copied whole, from and to 16-byte
-            # boundaries when Lx/2 is a multiple of 4
+            # its x coordinate (floats) is a multiple of 16 bytes
             assert 0 <= start and start + n <= vh
             assert (2 * start * 4) % 16 == 0 and 2 * n <= 256
-            assert start % lxh == 0 and n % lxh == 0
-            if lxh % 4 == 0:
-                assert (start // lxh * 52 * lxh) % 16 == 0 and (n * 52) % 16 == 0
         for s in range(T):
             i = geo[3] + s
             seen[i] += 1
@@ -244,29 +239,17 @@ def test_staged_layout_and_byte_count():
         if rows < 2:
             continue
         T = rows * lxh
-        assert T % 2 == 0
-        # (input site bytes, link bytes, link planes: (offset per site, width)),
-        # FP32 18 / 12, 16-bit 18 / 12, for the hop with the axpy addend
-        for sb, lb, planes in ((96, 72, [(0, 64), (64, 8)]), (96, 48, [(0, 48)]),
-                               (52, 36, [(0, 32), (32, 4)]), (52, 24, [(0, 16), (16, 8)])):
-            if sb == 52 and lxh % 4:
-                continue  # 16-bit row blocks need Lx/2 % 4 == 0 (then T % 4 == 0)
-            sizes = [sb * T, sb * lxh, sb * lxh] + [sb * T] * 4 + [8 * lb * T, 96 * T]
-            if sb < 96:
-                sizes.append(96 * T)  # partial sums need their own region
-            off, regions = 0, []
-            for b in sizes:
-                regions.append((off, off + b))
-                off += (b + 127) // 128 * 128
-            assert all(a % 128 == 0 for a, _ in regions)
-            assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
-            # every plane of every direction block starts on a 16-byte boundary
-            assert all((lb * T * d + o * T) % 16 == 0 for d in range(8) for o, _ in planes)
-            ring = {d: d * off + (2 * d + 8) * 8 for d in (2, 3, 4, 5)}
-            if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)) and want == 0:
-                assert ring[3] <= 227 * 1024, (lxh, ly, sb, lb)
-                if sb == 52:
-                    assert ring[4] <= 227 * 1024, (lxh, ly, sb, lb)
-            if (lxh, ly, want, sb, lb) == (16, 32, 2, 96, 72):
-                assert ring[5] <= 227 * 1024
-            assert sum(sizes) - (96 * T if sb < 96 else 0) == sb * (5 * T + 2 * lxh) + 8 * lb * T + 96 * T
+        sizes = [96 * T, 96 * lxh, 96 * lxh] + [96 * T] * 4 + [576 * T, 96 * T]
+        off, regions = 0, []
+        for b in sizes:
+            regions.append((off, off + b))
+            off += (b + 127) // 128 * 128
+        assert all(a % 128 == 0 for a, _ in regions)
+        assert all(regions[k][1] <= regions[k + 1][0] for k in range(len(regions) - 1))
+        assert all((72 * T * d) % 16 == 0 and (72 * T * d + 64 * T) % 16 == 0 for d in range(8))
+        ring = {d: d * off + (2 * d + 6) * 8 for d in (2, 3, 4, 5)}
+        if (lxh, ly) in ((16, 32), (24, 48), (12, 24), (8, 16), (4, 8)) and want == 0:
+            assert ring[3] <= 227 * 1024, (lxh, ly)
+        if (lxh, ly, want) == (16, 32, 2):
+            assert ring[5] <= 227 * 1024
+        assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 576 * T + 96 * T
