@@ -210,13 +210,9 @@ __device__ __forceinline__ int row_start(const StagedParams &P, int z, int t, in
 }
 
 // issue the loads of tile j into the stage at `base`
-// which copies of a tile to issue: all, the link block (with the stage's
-// byte count), or the spinor boxes
-enum IssuePart { ISSUE_ALL = 3, ISSUE_LINKS = 1, ISSUE_SPINORS = 2 };
-
 template <bool Axpy>
 __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *base, uint64_t *full,
-                                           uint64_t pol, int part)
+                                           uint64_t pol)
 {
     const TileGeo g = tile_geo(P, j);
     const StageLayout &L = P.L;
@@ -227,12 +223,9 @@ __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *b
     const int tp = g.t + 1 == lt ? 0 : g.t + 1, tm = g.t == 0 ? lt - 1 : g.t - 1;
     const int i0 = (int)g.i0;
     const int jt = (int)(g.i0 / P.tile);  // tile index in memory order
-    if (part & ISSUE_LINKS) {
-        mbar_expect_tx(full, (unsigned)L.tx);
-        // the links are read once per launch: evict first
-        bulk_hint(base + L.lk, P.links + (long long)jt * 576 * P.tile, (unsigned)(576 * P.tile), full, pol);
-    }
-    if (!(part & ISSUE_SPINORS)) return;
+    mbar_expect_tx(full, (unsigned)L.tx);
+    // the links are read once per launch: evict first
+    bulk_hint(base + L.lk, P.links + (long long)jt * 576 * P.tile, (unsigned)(576 * P.tile), full, pol);
     // input spinor (parity 1-p); the coordinate is in floats, 2 per complex
     tma_2d(base + L.sp[0], &P.sp_tile, 2 * i0, 0, full);
     tma_2d(base + L.sp[1], &P.sp_row, 2 * row_start(P, g.z, g.t, ym), 0, full);
@@ -310,9 +303,6 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // the next staged hop may be scheduled now: it loads only its link blocks
-    // (which no kernel writes) before it waits for this grid to complete
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 2 * NS * P.tpt) {  // producer
         if (lane != 0) return;
@@ -321,21 +311,13 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
         if (Axpy)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.x_tile)) : "memory");
         const uint64_t pol = policy_evict_first();
-        // link blocks of the first tiles while the previous kernel finishes;
-        // everything a kernel may write is read only after it has completed
-        const int pro = ntile_cta < NS ? ntile_cta : NS;
-        for (int k = 0; k < pro; ++k)
-            if (!(P.inject && k == 0))
-                issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + k * L.bytes, full + k,
-                                 pol, ISSUE_LINKS);
-        asm volatile("griddepcontrol.wait;" ::: "memory");
         int issued = 0;
         for (int k = 0; k < ntile_cta; ++k) {
             const int s = k % NS, n = k / NS;
             if (n >= 1 && !mbar_wait(empty + s, (unsigned)((n - 1) & 1), P)) break;
             if (P.inject && k == 0) continue;  // nothing loaded, nothing in flight
             issue_tile<Axpy>(P, (int)blockIdx.x + k * (int)gridDim.x, smem + s * L.bytes,
-                             full + s, pol, k < pro ? ISSUE_SPINORS : ISSUE_ALL);
+                             full + s, pol);
             issued = k + 1;
         }
         // the last loads of each stage must have landed before the CTA exits
@@ -358,8 +340,6 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     constexpr int S0 = Dag ? -1 : 1;
     const int st = g;
     char *base = smem + st * L.bytes;
-    // outputs are written only after the previous kernel has completed
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int k = g; k < ntile_cta; k += NS) {
         const unsigned m = (unsigned)(k / NS);  // use of this stage
         if (!mbar_wait(full + st, m & 1u, P)) return;
@@ -552,19 +532,8 @@ int launch_staged(const StagedParams &P, int grid, cudaStream_t s)
     });
     WEO_CUDA(attr);
     const int threads = 32 * (2 * NS * P.tpt + 1);  // NS x tpt teams and the producer
-    // programmatic dependent launch: this grid may start while the previous
-    // kernel on the stream drains (see griddepcontrol in the kernel)
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)threads);
-    cfg.dynamicSmemBytes = staged_smem(P.L, NS);
-    cfg.stream = s;
-    cudaLaunchAttribute pdl[1];
-    pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    pdl[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = pdl;
-    cfg.numAttrs = 1;
-    WEO_CUDA(cudaLaunchKernelEx(&cfg, hop_staged_kernel<Dag, Axpy, NS>, P));
+    hop_staged_kernel<Dag, Axpy, NS><<<grid, threads, staged_smem(P.L, NS), s>>>(P);
+    WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }
 
