@@ -9,8 +9,8 @@
 //     inside the tile), the rows y0-1 and y0+R (periodic in y), and the tile
 //     rows of the planes z+1, z-1, t+1, t-1 (periodic): seven boxes of the
 //     planar array, loaded with cp.async.bulk.tensor;
-//   links: the eight links of every output site -- U_mu(x) and U_mu(x-mu)^dag's
-//     source U_mu(x-mu) -- repacked once per gauge field into one block per
+//   links: the eight links of every output site -- U_mu(x), and U_mu(x-mu)
+//     whose adjoint the backward hop applies -- repacked once per gauge field into one block per
 //     tile (direction-major, planar inside), so a tile's links are a single
 //     cp.async.bulk copy. This doubles the links' footprint (each link is
 //     stored for both sites it joins), not their traffic: a hop still reads

@@ -223,3 +223,23 @@ def test_tuner_considers_the_staged_hop(weo, oracle_lib):
     if not st["staged"]:
         assert op.info()["device_bytes"] < 60 * 2**20  # the trial's link blocks (36 MiB) were released
     op.close()
+
+
+def test_staged_is_deterministic(weo):
+    """Fixed accumulation order (x/y half plus z/t half, per site): repeated
+    applies and applies on another stream give identical bits."""
+    import torch
+
+    dims = (32, 8, 8, 8)
+    U = to_device(gen.gauge_field(dims, "haar", seed=316))
+    x = to_device(to_planar(gen.gaussian_spinor(dims, seed=317)[0]), "f32")
+    op = weo.WilsonEO(dims, 0.13, U, prec="f32")
+    weo.wilson_eo_set_staging(op.handle, True)
+    y0 = op.apply(x)
+    s = torch.cuda.Stream()
+    for k in range(3):
+        y = op.apply(x) if k % 2 == 0 else op.apply(x, stream=s)
+        torch.cuda.synchronize()
+        assert torch.equal(y, y0)
+    weo.wilson_eo_check(op.handle)
+    op.close()
