@@ -145,8 +145,7 @@ int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, c
                cudaStream_t s)
 {
     const bool staged = h->cfg[prec].staged && prec == WEO_F32 && fmt == WEO_LINK18 &&
-                        io == IO_SAME && p.nrhs == 1 && staged_arrays_ok(p, axpy) &&
-                        staged_ready(h, p, s);
+                        io == IO_SAME && staged_arrays_ok(p, axpy) && staged_ready(h, p, s);
     int tok = -1;
     if (h->prof) {
         const char *kind = staged ? "hop_staged"

@@ -68,6 +68,18 @@ struct StagedParams {
     unsigned int *err;
     unsigned long long limit_ns;
     int inject;  // failure-path test: the producer never loads the CTA's first tile
+    // several right-hand sides (hop_staged_mrhs_kernel): the spinor maps are
+    // 3D (rhs outermost); output r at out + r * out_stride (complex)
+    int nrhs;
+    long long out_stride;
+};
+
+// shared memory of the multi-RHS kernel: two link slots (a tile's links stay
+// while all its right-hand sides pass) and a ring of spinor stages
+struct MrhsLayout {
+    int lk[2];   // link blocks of two tiles
+    int base;    // first spinor stage
+    StageLayout S;  // one spinor stage (S.lk unused)
 };
 
 int round128(int b) { return (b + 127) & ~127; }
@@ -181,6 +193,16 @@ __device__ __forceinline__ void bulk_hint(void *dst, const void *src, unsigned b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
         " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                       uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
         : "memory");
 }
 
@@ -421,6 +443,174 @@ __global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_kernel(const __g
     }
 }
 
+// Several right-hand sides: item k of a CTA is (tile m = k / nrhs, rhs r =
+// k % nrhs). A tile's link block is loaded once, into slot m % 2, and serves
+// all its right-hand sides; the spinor boxes of each item go through a ring of
+// NS stages owned by NS consumer groups (item k -> group k % NS). With
+// NS <= nrhs every group meets every tile, so each waiter again waits for the
+// phase right after the one it saw last.
+template <bool Dag, bool Axpy, int NS>
+__global__ void __launch_bounds__(kStagedThreads, 1) hop_staged_mrhs_kernel(const __grid_constant__ StagedParams P,
+                                                                           const __grid_constant__ MrhsLayout M)
+{
+    extern __shared__ __align__(128) char smem[];
+    const StageLayout &L = M.S;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + M.base + NS * L.bytes);
+    uint64_t *empty = full + NS;
+    uint64_t *lfull = empty + NS;  // link slots
+    uint64_t *lempty = lfull + 2;
+    uint64_t *ready = lempty + 2;  // per team
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int ntile_cta =
+        P.ntiles > (int)blockIdx.x ? (P.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nitems = ntile_cta * P.nrhs;
+    const int T = P.tile;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, (unsigned)P.tpt);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(lfull + s, 1);
+            mbar_init(lempty + s, (unsigned)(P.tpt * P.nrhs));  // every item of the tile
+        }
+        for (int t = 0; t < kTeams; ++t) mbar_init(ready + t, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == 2 * NS * P.tpt) {  // producer
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();
+        int issued = 0, tiles_issued = 0;
+        bool ok = true;
+        for (int k = 0; k < nitems && ok; ++k) {
+            const int m = k / P.nrhs, r = k - m * P.nrhs;
+            const TileGeo g = tile_geo(P, (int)blockIdx.x + m * (int)gridDim.x);
+            if (r == 0) {  // the tile's links, once
+                const int ls = m & 1, n = m >> 1;
+                if (n >= 1 && !mbar_wait(lempty + ls, (unsigned)((n - 1) & 1), P)) break;
+                mbar_expect_tx(lfull + ls, (unsigned)(576 * T));
+                bulk_hint(smem + M.lk[ls], P.links + (g.i0 / T) * 576 * T, (unsigned)(576 * T),
+                          lfull + ls, pol);
+                tiles_issued = m + 1;
+            }
+            const int st = k % NS, u = k / NS;
+            if (u >= 1 && !mbar_wait(empty + st, (unsigned)((u - 1) & 1), P)) break;
+            char *base = smem + M.base + st * L.bytes;
+            const int ly = P.ly, lz = P.lz, lt = P.lt;
+            const int ym = g.y0 == 0 ? ly - 1 : g.y0 - 1;
+            const int yp = g.y0 + P.rows == ly ? 0 : g.y0 + P.rows;
+            const int zp = g.z + 1 == lz ? 0 : g.z + 1, zm = g.z == 0 ? lz - 1 : g.z - 1;
+            const int tp = g.t + 1 == lt ? 0 : g.t + 1, tm = g.t == 0 ? lt - 1 : g.t - 1;
+            mbar_expect_tx(full + st, (unsigned)L.tx);
+            tma_3d(base + L.sp[0], &P.sp_tile, 2 * (int)g.i0, 0, r, full + st);
+            tma_3d(base + L.sp[1], &P.sp_row, 2 * row_start(P, g.z, g.t, ym), 0, r, full + st);
+            tma_3d(base + L.sp[2], &P.sp_row, 2 * row_start(P, g.z, g.t, yp), 0, r, full + st);
+            tma_3d(base + L.sp[3], &P.sp_tile, 2 * row_start(P, zp, g.t, g.y0), 0, r, full + st);
+            tma_3d(base + L.sp[4], &P.sp_tile, 2 * row_start(P, zm, g.t, g.y0), 0, r, full + st);
+            tma_3d(base + L.sp[5], &P.sp_tile, 2 * row_start(P, g.z, tp, g.y0), 0, r, full + st);
+            tma_3d(base + L.sp[6], &P.sp_tile, 2 * row_start(P, g.z, tm, g.y0), 0, r, full + st);
+            if (Axpy) tma_3d(base + L.x, &P.x_tile, 2 * (int)g.i0, 0, r, full + st);
+            issued = k + 1;
+        }
+        // the last loads of each stage and link slot must land before the CTA exits
+        for (int k = issued - 1; k >= 0 && k >= issued - NS; --k)
+            mbar_wait(full + k % NS, (unsigned)((k / NS) & 1), P);
+        for (int m = tiles_issued - 1; m >= 0 && m >= tiles_issued - 2; --m)
+            mbar_wait(lfull + (m & 1), (unsigned)((m >> 1) & 1), P);
+        return;
+    }
+
+    const int team = warp >> 1, q = warp & 1;
+    const int g = team / P.tpt;
+    const int s = (team - g * P.tpt) * 32 + lane;
+    const bool active = s < T;
+    const int lxh = P.lxh;
+    const int r0 = s / lxh, xh = s - r0 * lxh;
+    constexpr int S0 = Dag ? -1 : 1;
+    char *base = smem + M.base + g * L.bytes;
+    const float2 *sp0 = reinterpret_cast<const float2 *>(base + L.sp[0]);
+    float2 *part = reinterpret_cast<float2 *>(base + L.sp[3]);
+    const int ld4 = 18 * T / 4, ld2 = 9 * T;
+    for (int k = g; k < nitems; k += NS) {
+        const int m = k / P.nrhs, rhs = k - m * P.nrhs;
+        const unsigned u = (unsigned)(k / NS);
+        if (!mbar_wait(lfull + (m & 1), (unsigned)((m >> 1) & 1), P)) return;
+        if (!mbar_wait(full + g, u & 1u, P)) return;
+        const char *lk = smem + M.lk[m & 1];
+        const float4 *l4 = reinterpret_cast<const float4 *>(lk);
+        const float2 *l2 = reinterpret_cast<const float2 *>(lk + 64 * T);
+        const TileGeo tg = tile_geo(P, (int)blockIdx.x + m * (int)gridDim.x);
+        cx<float> acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = {0.f, 0.f};
+        if (q == 0) {
+            if (active) {
+                const int par = (tg.y0 + r0 + tg.z + tg.t + P.out_parity) & 1;
+                const int xp = par ? (xh + 1 == lxh ? 0 : xh + 1) : xh;
+                const int xm = par ? xh : (xh == 0 ? lxh - 1 : xh - 1);
+                const int rb = r0 * lxh;
+                staged_dir<0, true, S0>(acc, sp0, T, rb + xp, l4, l2, T, s);
+                staged_dir<0, false, S0>(acc, sp0, T, rb + xm, l4 + ld4, l2 + ld2, T, s);
+                if (r0 + 1 < P.rows)
+                    staged_dir<1, true, S0>(acc, sp0, T, rb + lxh + xh, l4 + 2 * ld4, l2 + 2 * ld2, T, s);
+                else
+                    staged_dir<1, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[2]),
+                                            lxh, xh, l4 + 2 * ld4, l2 + 2 * ld2, T, s);
+                if (r0 > 0)
+                    staged_dir<1, false, S0>(acc, sp0, T, rb - lxh + xh, l4 + 3 * ld4, l2 + 3 * ld2, T, s);
+                else
+                    staged_dir<1, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[1]),
+                                             lxh, xh, l4 + 3 * ld4, l2 + 3 * ld2, T, s);
+            }
+            if (!mbar_wait(ready + team, u & 1u, P)) return;
+            if (active) {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    const float2 v = part[c * T + s];
+                    acc[c].r += v.x;
+                    acc[c].i += v.y;
+                }
+                float2 *out = P.out + rhs * P.out_stride + tg.i0 + s;
+                if (Axpy) {
+                    const float2 *xv = reinterpret_cast<const float2 *>(base + L.x);
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) {
+                        const float2 v = xv[c * T + s];
+                        out[c * P.vh] = make_float2(fmaf(P.a, acc[c].r, v.x), fmaf(P.a, acc[c].i, v.y));
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) out[c * P.vh] = make_float2(acc[c].r, acc[c].i);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(empty + g);
+                mbar_arrive(lempty + (m & 1));
+            }
+        } else {
+            if (active) {
+                staged_dir<2, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[3]), T, s,
+                                        l4 + 4 * ld4, l2 + 4 * ld2, T, s);
+                staged_dir<2, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[4]), T, s,
+                                         l4 + 5 * ld4, l2 + 5 * ld2, T, s);
+                staged_dir<3, true, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[5]), T, s,
+                                        l4 + 6 * ld4, l2 + 6 * ld2, T, s);
+                staged_dir<3, false, S0>(acc, reinterpret_cast<const float2 *>(base + L.sp[6]), T, s,
+                                         l4 + 7 * ld4, l2 + 7 * ld2, T, s);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) part[c * T + s] = make_float2(acc[c].r, acc[c].i);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ready + team);
+        }
+    }
+}
+
 // ----------------------------------------------------------- link blocks --
 // Link block of output parity p for tile size T: for output site i (tile
 // i / T, site s = i % T), direction d = 2 mu + b holds U_mu(x) (b = 0) or
@@ -537,6 +727,52 @@ int launch_staged(const StagedParams &P, int grid, cudaStream_t s)
     return WEO_OK;
 }
 
+// multi-RHS layout: two link slots, then `stages` spinor stages (no link
+// region inside a stage); mbarriers after them
+size_t mrhs_smem(const MrhsLayout &M, int stages)
+{
+    return (size_t)M.base + (size_t)stages * M.S.bytes + (2 * stages + 4 + kTeams) * sizeof(uint64_t);
+}
+
+void make_mrhs_layout(int lxh, int rows, bool axpy, MrhsLayout &M)
+{
+    const int T = lxh * rows;
+    M.lk[0] = 0;
+    M.lk[1] = round128(576 * T);
+    M.base = 2 * round128(576 * T);
+    StageLayout &L = M.S;
+    int off = 0;
+    auto take = [&](int bytes) {
+        const int o = off;
+        off += round128(bytes);
+        return o;
+    };
+    L.sp[0] = take(96 * T);
+    L.sp[1] = take(96 * lxh);
+    L.sp[2] = take(96 * lxh);
+    for (int k = 3; k < 7; ++k) L.sp[k] = take(96 * T);
+    L.lk = 0;
+    L.x = axpy ? take(96 * T) : 0;
+    L.bytes = off;
+    L.tx = 5 * 96 * T + 2 * 96 * lxh + (axpy ? 96 * T : 0);
+}
+
+template <bool Dag, bool Axpy, int NS>
+int launch_mrhs(const StagedParams &P, const MrhsLayout &M, int grid, cudaStream_t s)
+{
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(hop_staged_mrhs_kernel<Dag, Axpy, NS>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    });
+    WEO_CUDA(attr);
+    const int threads = 32 * (2 * NS * P.tpt + 1);
+    hop_staged_mrhs_kernel<Dag, Axpy, NS><<<grid, threads, mrhs_smem(M, NS), s>>>(P, M);
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
 template <int NS>
 int launch_depth(bool dag, bool axpy, const StagedParams &P, int grid, cudaStream_t s)
 {
@@ -642,12 +878,17 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     make_layout(lxh, rows, axpy, P.L);
     const long long vh = p.vh;
     const int T = rows * lxh;
-    // spinor: 12 planes of 2 vh floats
-    const cuuint64_t sd[2] = {(cuuint64_t)(2 * vh), 12};
-    const cuuint64_t ss[1] = {(cuuint64_t)(8 * vh)};
-    const cuuint32_t b_tile[2] = {(cuuint32_t)(2 * T), 12}, b_row[2] = {(cuuint32_t)(2 * lxh), 12};
-    bool ok = encode(&P.sp_tile, p.in, 2, sd, ss, b_tile) && encode(&P.sp_row, p.in, 2, sd, ss, b_row);
-    if (ok && axpy) ok = encode(&P.x_tile, p.x, 2, sd, ss, b_tile);
+    const int nrhs = p.nrhs;
+    // spinor: [rhs][12 planes][2 vh floats]; one right-hand side: 2D maps
+    const cuuint64_t sd[3] = {(cuuint64_t)(2 * vh), 12, (cuuint64_t)nrhs};
+    const cuuint64_t ss[2] = {(cuuint64_t)(8 * vh), (cuuint64_t)p.in_stride};
+    const cuuint64_t sx[2] = {(cuuint64_t)(8 * vh), (cuuint64_t)p.x_stride};
+    const cuuint32_t b_tile[3] = {(cuuint32_t)(2 * T), 12, 1}, b_row[3] = {(cuuint32_t)(2 * lxh), 12, 1};
+    const int rank = nrhs > 1 ? 3 : 2;
+    if (nrhs > 1 && ((p.in_stride & 15) || (axpy && (p.x_stride & 15)) || (p.out_stride & 7)))
+        return set_error(WEO_ERR_UNSUPPORTED, "staged hop: right-hand-side strides not aligned");
+    bool ok = encode(&P.sp_tile, p.in, rank, sd, ss, b_tile) && encode(&P.sp_row, p.in, rank, sd, ss, b_row);
+    if (ok && axpy) ok = encode(&P.x_tile, p.x, rank, sd, sx, b_tile);
     if (!ok) return set_error(WEO_ERR_CUDA, "staged hop: tensor map encoding failed");
     P.links = blocks + (long long)p.out_parity * 576 * vh;
     P.lxh = lxh;
@@ -669,6 +910,22 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     int sms = 0;
     WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     const int grid = P.ntiles < sms ? P.ntiles : sms;
+    if (nrhs > 1) {
+        // links once per tile for all right-hand sides; spinor ring of 2 or 3
+        P.nrhs = nrhs;
+        P.out_stride = p.out_stride / 8;
+        MrhsLayout M;
+        make_mrhs_layout(lxh, rows, axpy, M);
+        int ns = nrhs < 3 ? nrhs : 3;
+        while (ns > 2 && (mrhs_smem(M, ns) > kSmemLimit || ns * P.tpt > kTeams)) --ns;
+        if (mrhs_smem(M, ns) > kSmemLimit || ns * P.tpt > kTeams)
+            return set_error(WEO_ERR_UNSUPPORTED, "staged hop: multi-RHS ring does not fit");
+        if (ns == 2)
+            return dag ? (axpy ? launch_mrhs<true, true, 2>(P, M, grid, s) : launch_mrhs<true, false, 2>(P, M, grid, s))
+                       : (axpy ? launch_mrhs<false, true, 2>(P, M, grid, s) : launch_mrhs<false, false, 2>(P, M, grid, s));
+        return dag ? (axpy ? launch_mrhs<true, true, 3>(P, M, grid, s) : launch_mrhs<true, false, 3>(P, M, grid, s))
+                   : (axpy ? launch_mrhs<false, true, 3>(P, M, grid, s) : launch_mrhs<false, false, 3>(P, M, grid, s));
+    }
     switch (depth) {
     case 2: return launch_depth<2>(dag, axpy, P, grid, s);
     case 3: return launch_depth<3>(dag, axpy, P, grid, s);

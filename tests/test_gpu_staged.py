@@ -131,8 +131,9 @@ def test_staged_rejects_ineligible_lattices(weo, dims, prec, fmt):
 
 
 def test_staged_other_formats_keep_the_default_kernel(weo, oracle_lib):
-    """Staging on, but 12-real links / FP16 storage / two right-hand sides: the
-    default kernels run and the results stay correct."""
+    """Staging on, but 12-real links / FP16 storage: the default kernels run;
+    FP32 18-real links with two right-hand sides take the multi-RHS staged
+    kernel. Results stay correct."""
     dims = (8, 8, 8, 8)
     U = gen.gauge_field(dims, "smooth", seed=306, eps=0.4)
     psi = gen.gaussian_spinor(dims, nrhs=2, seed=307)
@@ -242,4 +243,53 @@ def test_staged_is_deterministic(weo):
         torch.cuda.synchronize()
         assert torch.equal(y, y0)
     weo.wilson_eo_check(op.handle)
+    op.close()
+
+
+@pytest.mark.parametrize("dims,nrhs", [((8, 8, 8, 8), 2), ((16, 16, 16, 16), 3), ((16, 8, 4, 6), 5),
+                                       ((16, 16, 16, 16), 12), ((4, 4, 4, 4), 7)])
+def test_staged_multi_rhs_matches_oracle(weo, oracle_lib, dims, nrhs):
+    """Several right-hand sides: each tile's link block is loaded once and
+    serves every right-hand side (rings of 2 or 3 spinor stages), for M_eo,
+    M_eo^dag and single hops of both parities, against the oracle and the
+    default multi-RHS kernels."""
+    U = gen.gauge_field(dims, "haar", seed=318)
+    psi = gen.gaussian_spinor(dims, nrhs=nrhs, seed=319)
+    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
+    x = to_device(to_planar(psi), "f32")
+    ref = {d: op.apply(x, dag=d) for d in (False, True)}
+    href = op.hop(x, 1)
+    weo.wilson_eo_set_staging(op.handle, True)
+    for dag in (False, True):
+        y = op.apply(x, dag=dag)
+        weo.wilson_eo_check(op.handle)
+        f = oracle_lib.meo_dag if dag else oracle_lib.meo
+        for r in range(nrhs):
+            assert rel_l2(from_planar(y[r].cpu().numpy()), f(U, 0.13, psi[r], dims)) <= TOL["f32"]
+        assert rel_l2(y.cpu().numpy(), ref[dag].cpu().numpy()) <= 1e-6
+    h = op.hop(x, 1)
+    weo.wilson_eo_check(op.handle)
+    assert rel_l2(h.cpu().numpy(), href.cpu().numpy()) <= 1e-6
+    op.close()
+
+
+def test_staged_multi_rhs_full_size_sampled(weo, oracle_lib):
+    """32^3 x 64 with 12 point-source-like right-hand sides (Gaussian here),
+    sampled sites of every right-hand side against the oracle."""
+    import torch
+
+    dims = (32, 32, 32, 64)
+    vh = int(np.prod(dims)) // 2
+    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    psi = gen.gaussian_spinor(dims, nrhs=12, seed=320)
+    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
+    weo.wilson_eo_set_staging(op.handle, True)
+    x = to_device(to_planar(psi), "f32")
+    y = op.apply(x)
+    weo.wilson_eo_check(op.handle)
+    sites = np.sort(gen.rng(4).choice(vh, 60, replace=False))
+    got = from_planar(y[:, :, :, torch.from_numpy(sites).cuda()].cpu().numpy())
+    for r in (0, 5, 11):
+        want = oracle_lib.meo_sites(U, 0.13, psi[r], dims, sites)
+        assert rel_l2(got[r], want) <= TOL["f32"]
     op.close()

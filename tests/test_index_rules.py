@@ -253,3 +253,109 @@ def test_staged_layout_and_byte_count():
         if (lxh, ly, want) == (16, 32, 2):
             assert ring[5] <= 227 * 1024
         assert sum(sizes) == 5 * 96 * T + 2 * 96 * lxh + 576 * T + 96 * T
+
+
+# ------------------------------------------------- staged barrier protocol --
+# mbarrier.try_wait.parity(P) succeeds when the phase of parity P has completed,
+# i.e. when P differs from the parity of the phase in progress. A waiter that
+# means phase n is therefore only right if the barrier is in phase n or n + 1
+# when it tests. This simulates the multi-RHS staged kernel's producer, its
+# link slots, its spinor ring and its consumer warps under random schedules
+# and checks that condition at every test, and that every schedule finishes.
+
+class _Barrier:
+    def __init__(self, count):
+        self.count, self.pending, self.phase = count, count, 0
+
+    def arrive(self):
+        self.pending -= 1
+        if self.pending == 0:
+            self.phase += 1
+            self.pending = self.count
+
+
+def _simulate_mrhs(ntiles, nrhs, ns, tpt, seed, land_p=0.3):
+    rnd = np.random.default_rng(seed)
+    full = [_Barrier(1) for _ in range(ns)]
+    empty = [_Barrier(tpt) for _ in range(ns)]
+    lfull = [_Barrier(1) for _ in range(2)]
+    lempty = [_Barrier(tpt * nrhs) for _ in range(2)]
+    ready = [_Barrier(1) for _ in range(ns * tpt)]
+    nitems = ntiles * nrhs
+    in_flight = []  # loads whose bytes have not landed: barriers to arrive on
+
+    def test(bar, n):
+        assert bar.phase in (n, n + 1), (bar.phase, n)
+        return (n & 1) != (bar.phase & 1)
+
+    def producer():
+        for k in range(nitems):
+            m, r = divmod(k, nrhs)
+            if r == 0:
+                if m >= 2:
+                    while not test(lempty[m & 1], (m >> 1) - 1):
+                        yield
+                in_flight.append(lfull[m & 1])
+            st, u = k % ns, k // ns
+            if u >= 1:
+                while not test(empty[st], u - 1):
+                    yield
+            in_flight.append(full[st])
+            yield
+
+    def consumer(team, q):
+        g = team // tpt
+        for k in range(g, nitems, ns):
+            m, u = k // nrhs, k // ns
+            while not test(lfull[m & 1], m >> 1):
+                yield
+            while not test(full[g], u):
+                yield
+            yield  # compute
+            if q == 1:
+                ready[team].arrive()
+            else:
+                while not test(ready[team], u):
+                    yield
+                empty[g].arrive()
+                lempty[m & 1].arrive()
+            yield
+
+    actors = [producer()] + [consumer(t, q) for t in range(ns * tpt) for q in (0, 1)]
+    live = list(range(len(actors)))
+    steps = 0
+    while live or in_flight:
+        steps += 1
+        assert steps < 200000, "no progress"
+        if in_flight and (not live or rnd.random() < land_p):
+            in_flight.pop(int(rnd.integers(len(in_flight)))).arrive()
+            continue
+        if not live:
+            continue
+        a = live[int(rnd.integers(len(live)))]
+        try:
+            next(actors[a])
+        except StopIteration:
+            live.remove(a)
+    return steps
+
+
+@pytest.mark.parametrize("ntiles,nrhs,ns,tpt", [(5, 2, 2, 1), (7, 3, 3, 2), (6, 12, 3, 2),
+                                               (4, 5, 3, 1), (9, 4, 2, 2), (3, 3, 3, 1)])
+def test_staged_mrhs_barrier_protocol(ntiles, nrhs, ns, tpt):
+    for seed in range(40):
+        for land_p in (0.03, 0.3):  # loads that linger, loads that land at once
+            _simulate_mrhs(ntiles, nrhs, ns, tpt, seed, land_p)
+
+
+def test_staged_mrhs_protocol_check_catches_a_ring_deeper_than_nrhs():
+    """A planted mistake: three consumer groups for two right-hand sides lets
+    a group skip a tile and test a link slot two phases ahead; the simulation
+    must notice."""
+    caught = 0
+    for seed in range(60):
+        try:
+            _simulate_mrhs(8, 2, 3, 1, seed, 0.03)
+        except AssertionError:
+            caught += 1
+    assert caught > 0
