@@ -298,6 +298,11 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
  * not 16-byte aligned fall back to the default kernel. Waits are bounded
  * (about a second); a wait that gives up is reported by wilson_eo_check as
  * WEO_ERR_TIMEOUT. staged = 0 (default) restores the default kernel.
+ * staged = 2 also stages multi-RHS hops: each tile's link block is loaded once
+ * into one of two link slots and serves every right-hand side, whose spinor
+ * boxes pass through a ring of 2-3 stages (measured slower than two right-hand
+ * sides per thread at 12 right-hand sides on 32^3 x 64, 11.6 vs 13.7 TFlop/s,
+ * so staged = 1 leaves multi-RHS hops to the default kernels).
  * rows: lattice rows R per tile (0: the largest that qualifies); depth: stages
  * of the ring, 2..5 (0: the most up to 3 that fit). A tile of R Lx/2 sites is
  * computed by one or two teams of two warps (x/y and z/t directions, 32 sites

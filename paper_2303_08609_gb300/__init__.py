@@ -481,9 +481,10 @@ def wilson_eo_inject_fused_timeout(h, out_e, in_e, stream=None):
 
 def wilson_eo_set_staging(h, staged=True, rows=0, depth=0):
     """Hops of FP32 18-real operators fed by TMA through a shared-memory ring
-    (True) or the default one-site-per-thread kernel (False); rows per tile and
-    ring depth, 0 for automatic."""
-    _check(_load().wilson_eo_set_staging(h, int(bool(staged)), int(rows), int(depth)),
+    (True or 1: single-RHS hops; 2: multi-RHS hops too) or the default
+    one-site-per-thread kernel (False); rows per tile and ring depth, 0 for
+    automatic."""
+    _check(_load().wilson_eo_set_staging(h, int(staged), int(rows), int(depth)),
            "wilson_eo_set_staging")
 
 
@@ -493,7 +494,7 @@ def wilson_eo_get_staging(h):
     v, r, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(_load().wilson_eo_get_staging(h, ctypes.byref(v), ctypes.byref(r), ctypes.byref(d)),
            "wilson_eo_get_staging")
-    return {"staged": bool(v.value), "rows": r.value, "depth": d.value}
+    return {"staged": v.value, "rows": r.value, "depth": d.value}
 
 
 def wilson_eo_inject_staged_timeout(h, out_o, in_e, stream=None):

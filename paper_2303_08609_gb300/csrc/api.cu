@@ -144,7 +144,9 @@ static int upload_gauge(wilson_eo_s *h, const void *gauge, int gauge_is_f64, cud
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
                cudaStream_t s)
 {
-    const bool staged = h->cfg[prec].staged && prec == WEO_F32 && fmt == WEO_LINK18 &&
+    // staged 1: single-RHS hops; 2: multi-RHS hops too
+    const int sm = h->cfg[prec].staged;
+    const bool staged = (p.nrhs == 1 ? sm >= 1 : sm == 2) && prec == WEO_F32 && fmt == WEO_LINK18 &&
                         io == IO_SAME && staged_arrays_ok(p, axpy) && staged_ready(h, p, s);
     int tok = -1;
     if (h->prof) {
@@ -381,7 +383,7 @@ int wilson_eo_set_staging(wilson_eo_t h, int staged, int rows, int depth)
 {
     try {
         if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
-        if (staged != 0 && staged != 1) return set_error(WEO_ERR_ARG, "staged must be 0 or 1");
+        if (staged < 0 || staged > 2) return set_error(WEO_ERR_ARG, "staged must be 0, 1 or 2");
         if (rows < 0 || depth < 0 || depth == 1 || depth > 5)
             return set_error(WEO_ERR_ARG, "rows >= 0, depth 0 or 2..5");
         const int old_rows = h->staged_rows, old_depth = h->staged_depth;

@@ -124,16 +124,16 @@ def test_staged_rejects_ineligible_lattices(weo, dims, prec, fmt):
         with pytest.raises(weo.WilsonEOError) as e:
             weo.wilson_eo_set_staging(op.handle, True)
         assert e.value.status == -3
-        assert weo.wilson_eo_get_staging(op.handle) == {"staged": False, "rows": 0, "depth": 0}
+        assert weo.wilson_eo_get_staging(op.handle) == {"staged": 0, "rows": 0, "depth": 0}
     else:
         weo.wilson_eo_set_staging(op.handle, True)
     op.close()
 
 
 def test_staged_other_formats_keep_the_default_kernel(weo, oracle_lib):
-    """Staging on, but 12-real links / FP16 storage: the default kernels run;
-    FP32 18-real links with two right-hand sides take the multi-RHS staged
-    kernel. Results stay correct."""
+    """Staging on, but 12-real links / FP16 storage / two right-hand sides
+    (multi-RHS hops are staged only with staged = 2): the default kernels run
+    and the results stay correct."""
     dims = (8, 8, 8, 8)
     U = gen.gauge_field(dims, "smooth", seed=306, eps=0.4)
     psi = gen.gaussian_spinor(dims, nrhs=2, seed=307)
@@ -183,7 +183,7 @@ def test_staged_tile_and_ring_shapes(weo, oracle_lib, rows, depth):
     psi = gen.gaussian_spinor(dims, seed=311)[0]
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
     weo.wilson_eo_set_staging(op.handle, True, rows, depth)
-    assert weo.wilson_eo_get_staging(op.handle) == {"staged": True, "rows": rows, "depth": depth}
+    assert weo.wilson_eo_get_staging(op.handle) == {"staged": 1, "rows": rows, "depth": depth}
     x = to_device(to_planar(psi), "f32")
     for dag in (False, True):
         y = op.apply(x, dag=dag)
@@ -203,7 +203,7 @@ def test_staged_rejects_shapes_that_do_not_fit(weo):
     with pytest.raises(weo.WilsonEOError) as e:
         weo.wilson_eo_set_staging(op.handle, True, 0, 6)
     assert e.value.status == -1
-    assert weo.wilson_eo_get_staging(op.handle) == {"staged": False, "rows": 4, "depth": 3}
+    assert weo.wilson_eo_get_staging(op.handle) == {"staged": 0, "rows": 4, "depth": 3}
     op.close()
 
 
@@ -259,7 +259,7 @@ def test_staged_multi_rhs_matches_oracle(weo, oracle_lib, dims, nrhs):
     x = to_device(to_planar(psi), "f32")
     ref = {d: op.apply(x, dag=d) for d in (False, True)}
     href = op.hop(x, 1)
-    weo.wilson_eo_set_staging(op.handle, True)
+    weo.wilson_eo_set_staging(op.handle, 2)
     for dag in (False, True):
         y = op.apply(x, dag=dag)
         weo.wilson_eo_check(op.handle)
@@ -283,7 +283,7 @@ def test_staged_multi_rhs_full_size_sampled(weo, oracle_lib):
     U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
     psi = gen.gaussian_spinor(dims, nrhs=12, seed=320)
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
-    weo.wilson_eo_set_staging(op.handle, True)
+    weo.wilson_eo_set_staging(op.handle, 2)
     x = to_device(to_planar(psi), "f32")
     y = op.apply(x)
     weo.wilson_eo_check(op.handle)
