@@ -234,9 +234,9 @@ static int apply_common(wilson_eo_t h, void *out_e, const void *in_e, int nrhs, 
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = ext_spinor_bytes(h) * (size_t)nrhs;
-    const void *in;
-    void *out;
-    bool out_host;
+    const void *in = nullptr;
+    void *out = nullptr;
+    bool out_host = false;
     WEO_TRY(stage_in(h->stage_in, in_e, bytes, s, &in));
     WEO_TRY(stage_out(h->stage_out, out_e, bytes, &out, &out_host));
     WEO_TRY(meo_device(h, out, in, nrhs, dag, s));
@@ -252,9 +252,9 @@ static int apply_ff_common(wilson_eo_t h, void *out_e, const void *in_e, int nrh
     DeviceGuard g(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)h->vh * 192 * (size_t)nrhs;  // complex128 and float-float alike
-    const void *in;
-    void *out;
-    bool out_host;
+    const void *in = nullptr;
+    void *out = nullptr;
+    bool out_host = false;
     WEO_TRY(stage_in(h->stage_in, in_e, bytes, s, &in));
     WEO_TRY(stage_out(h->stage_out, out_e, bytes, &out, &out_host));
     const PackedGauge *gf = nullptr;
@@ -553,9 +553,9 @@ int wilson_eo_hop(wilson_eo_t h, int out_parity, int dag, void *out, const void 
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t ext = ext_spinor_bytes(h);
         const size_t bytes = ext * (size_t)nrhs;
-        const void *din;
-        void *dout;
-        bool out_host;
+        const void *din = nullptr;
+        void *dout = nullptr;
+        bool out_host = false;
         WEO_TRY(stage_in(h->stage_in, in, bytes, s, &din));
         WEO_TRY(stage_out(h->stage_out, out, bytes, &dout, &out_host));
         HopParams p = geom_params(h);
@@ -585,9 +585,9 @@ int wilson_eo_link_grad(wilson_eo_t h, void *grad, const void *g_e, const void *
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t sb = ext_spinor_bytes(h);
         const size_t gb = (size_t)(2 * h->vh) * 4 * 9 * (h->prec == WEO_F64 ? 16 : 8);
-        const void *g, *phi;
-        void *out;
-        bool out_host;
+        const void *g = nullptr, *phi = nullptr;
+        void *out = nullptr;
+        bool out_host = false;
         WEO_TRY(stage_in(h->stage_in, g_e, sb, s, &g));
         WEO_TRY(stage_in(h->even1, phi_e, sb, s, &phi));
         WEO_TRY(stage_out(h->stage_aux, grad, gb, &out, &out_host));
@@ -608,9 +608,9 @@ int wilson_eo_force(wilson_eo_t h, void *force, void *dS_dphi_e, const void *phi
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t sb = ext_spinor_bytes(h);
         const size_t gb = (size_t)(2 * h->vh) * 4 * 9 * (h->prec == WEO_F64 ? 16 : 8);
-        const void *phi;
-        void *out, *dphi = nullptr;
-        bool out_host, dphi_host = false;
+        const void *phi = nullptr;
+        void *out = nullptr, *dphi = nullptr;
+        bool out_host = false, dphi_host = false;
         WEO_TRY(stage_in(h->stage_in, phi_e, sb, s, &phi));
         WEO_TRY(stage_out(h->stage_aux, force, gb, &out, &out_host));
         if (dS_dphi_e) WEO_TRY(stage_out(h->stage_out, dS_dphi_e, sb, &dphi, &dphi_host));
@@ -680,9 +680,9 @@ static int source_op(wilson_eo_t h, void *out, const void *in_a, const void *in_
     DeviceGuard dg(h->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t b = ext_spinor_bytes(h);
-    const void *a, *c;
-    void *o;
-    bool oh;
+    const void *a = nullptr, *c = nullptr;
+    void *o = nullptr;
+    bool oh = false;
     WEO_TRY(stage_in(h->stage_in, in_a, b, s, &a));
     WEO_TRY(stage_in(h->even1, in_b, b, s, &c));
     WEO_TRY(stage_out(h->stage_out, out, b, &o, &oh));

@@ -812,7 +812,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
 
 int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs)
 {
-    SolverState *S;
+    SolverState *S = nullptr;
     WEO_TRY(solver_state(h, &S));
     if (delta > 0.0 && delta < 1.0) S->delta = delta;
     if (chunk >= 1) S->chunk = chunk;
@@ -830,7 +830,7 @@ int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b
                  cudaStream_t user)
 {
     if (nrhs < 1 || nrhs > kMaxRhs) return set_error(WEO_ERR_ARG, "nrhs must be in 1..64");
-    SolverState *S;
+    SolverState *S = nullptr;
     WEO_TRY(solver_state(h, &S));
     S->nrhs = nrhs;
     const size_t b64 = (size_t)12 * h->vh * 16 * nrhs;
@@ -875,7 +875,7 @@ int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi
 int solver_residual_mode(wilson_eo_s *h, int mode)
 {
     if (mode != 0 && mode != 1) return set_error(WEO_ERR_ARG, "mode must be 0 (FP64) or 1 (float-float)");
-    SolverState *S;
+    SolverState *S = nullptr;
     WEO_TRY(solver_state(h, &S));
     S->ff_residual = mode;
     return WEO_OK;
@@ -924,7 +924,7 @@ int solve_full_device(wilson_eo_s *h, void *xi_e, void *xi_o, const void *eta_e,
                       const void *eta_o, const bool host[4], double tol, int maxiter, int mixed,
                       int *iters_out, double *relres_out, cudaStream_t user)
 {
-    SolverState *S;
+    SolverState *S = nullptr;
     WEO_TRY(solver_state(h, &S));
     cudaStream_t s = S->stream;
     const size_t b64 = (size_t)12 * h->vh * 16;
