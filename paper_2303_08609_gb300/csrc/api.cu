@@ -288,7 +288,7 @@ int wilson_eo_create(wilson_eo_t *out, const int dims[4], double kappa, int prec
     try {
         if (!out) return set_error(WEO_ERR_ARG, "out is NULL");
         *out = nullptr;
-        long long vh;
+        long long vh = 0;
         WEO_TRY(check_dims(dims, &vh));
         if (prec < WEO_F64 || prec > WEO_BF16) return set_error(WEO_ERR_ARG, "unknown precision");
         if (linkfmt != WEO_LINK18 && linkfmt != WEO_LINK12)
