@@ -359,3 +359,79 @@ def test_staged_mrhs_protocol_check_catches_a_ring_deeper_than_nrhs():
         except AssertionError:
             caught += 1
     assert caught > 0
+
+
+def _simulate_single(ntiles, ns, tpt, seed, land_p=0.3, groups=None):
+    """The one-right-hand-side staged kernel: stage g owned by group g (tiles
+    k = g, g + ns, ...), one load per tile (links and spinors). `groups` >
+    ns plants the first design's mistake (groups sharing stages)."""
+    rnd = np.random.default_rng(seed)
+    G = groups or ns
+    full = [_Barrier(1) for _ in range(ns)]
+    empty = [_Barrier(tpt) for _ in range(ns)]
+    ready = [_Barrier(1) for _ in range(G * tpt)]
+    in_flight = []
+
+    def test(bar, n):
+        assert bar.phase in (n, n + 1), (bar.phase, n)
+        return (n & 1) != (bar.phase & 1)
+
+    def producer():
+        for k in range(ntiles):
+            st, n = k % ns, k // ns
+            if n >= 1:
+                while not test(empty[st], n - 1):
+                    yield
+            in_flight.append(full[st])
+            yield
+
+    def consumer(team, q):
+        g = team // tpt
+        for m, k in enumerate(range(g, ntiles, G)):
+            st = k % ns
+            while not test(full[st], k // ns):
+                yield
+            yield
+            if q == 1:
+                ready[team].arrive()
+            else:
+                while not test(ready[team], m):
+                    yield
+                empty[st].arrive()
+            yield
+
+    actors = [producer()] + [consumer(t, q) for t in range(G * tpt) for q in (0, 1)]
+    live = list(range(len(actors)))
+    steps = 0
+    while live or in_flight:
+        steps += 1
+        assert steps < 200000, "no progress"
+        if in_flight and (not live or rnd.random() < land_p):
+            in_flight.pop(int(rnd.integers(len(in_flight)))).arrive()
+            continue
+        if not live:
+            continue
+        a = live[int(rnd.integers(len(live)))]
+        try:
+            next(actors[a])
+        except StopIteration:
+            live.remove(a)
+
+
+@pytest.mark.parametrize("ntiles,ns,tpt", [(7, 3, 2), (20, 3, 2), (11, 5, 1), (4, 2, 1), (2, 3, 2)])
+def test_staged_single_rhs_barrier_protocol(ntiles, ns, tpt):
+    for seed in range(40):
+        for land_p in (0.03, 0.3):
+            _simulate_single(ntiles, ns, tpt, seed, land_p)
+
+
+def test_staged_protocol_check_catches_groups_sharing_stages():
+    """The first design had six groups over two or three stages; the check
+    must reject it (the GPU test saw its bounded wait run out)."""
+    caught = 0
+    for seed in range(60):
+        try:
+            _simulate_single(16, 2, 1, seed, 0.03, groups=6)
+        except AssertionError:
+            caught += 1
+    assert caught > 0
