@@ -45,6 +45,14 @@ MUTANTS = {
                                   "        if (parity_of(c) == out_parity) continue;\n        hop_site("),
     "gradient with the wrong projector": ("projector(mu, -1, Pm); /* 1 - gamma_mu */",
                                           "projector(mu, +1, Pm); /* 1 - gamma_mu */"),
+    # the site-by-site M_eo that checks the full-size lattices
+    "sites: kappa not squared": ("out[12 * n + k] = in[12 * (x / 2) + k] - kappa * kappa * acc[k];",
+                                 "out[12 * n + k] = in[12 * (x / 2) + k] - kappa * acc[k];"),
+    "sites: adjoint's backward link taken at x": (
+        "apply_block(Pf, U + 9 * (mu * V + yb), 0, 1, tb[mu], acc);",
+        "apply_block(Pf, U + 9 * (mu * V + x), 0, 1, tb[mu], acc);"),
+    "sites: odd site for an even index": ("return parity_of(c) == 0 ? 2 * i : 2 * i + 1;",
+                                          "return parity_of(c) == 1 ? 2 * i : 2 * i + 1;"),
 }
 
 
@@ -60,6 +68,7 @@ def _pins(o):
         ("link gradient FD", lambda: pins.test_link_grad_finite_differences(o)),
         ("force FD", lambda: pins.test_force_finite_differences(o)),
         ("CG vs dense", lambda: pins.test_cg_against_dense_normal_equations(o)),
+        ("M_eo site by site vs full", lambda: pins.test_meo_sites_matches_full(o)),
     ]
 
 
