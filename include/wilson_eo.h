@@ -287,11 +287,15 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
 /* Hopping kernel fed by TMA (Eq. 1 for one parity, as wilson_eo_hop; used by
  * every hop of M_eo, M_eo^dag, the solvers and the force whose spinors are FP32
  * with 18-real FP32 links and one right-hand side). staged = 1: the output
- * sites are cut into tiles of R lattice rows; one producer warp per CTA loads
- * each tile's neighbour-spinor rows (same plane, y-1 / y+R rows, planes z+-1
- * and t+-1), its eight link rows and the axpy addend as cp.async.bulk.tensor
- * boxes into a ring of shared-memory stages, and consumer warps compute from
- * shared memory. Same arithmetic per direction as the default kernel; the
+ * sites are cut into tiles of R lattice rows; one producer thread per CTA
+ * loads each tile's neighbour-spinor rows (same plane, y-1 / y+R rows, planes
+ * z+-1 and t+-1) and the axpy addend as cp.async.bulk.tensor boxes, and the
+ * tile's eight links per site as one cp.async.bulk copy of a link block, into
+ * a ring of shared-memory stages; consumer warps compute from shared memory.
+ * The link blocks are repacked from the handle's field when staging is turned
+ * on and after wilson_eo_set_gauge (2 x 576 bytes per output site: 1.2 GB at
+ * 32^3 x 64; each link is stored for both sites it joins; released by
+ * staged = 0 and wilson_eo_destroy). Same arithmetic per direction as the default kernel; the
  * x/y and z/t halves of the sum are added at the end, so results agree to
  * FP32 rounding, not bitwise. Needs Lx/2 even and some R >= 2 dividing Ly with
  * R * Lx/2 <= 64 (WEO_ERR_UNSUPPORTED otherwise); arrays whose addresses are
