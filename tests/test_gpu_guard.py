@@ -116,3 +116,33 @@ def test_link_gradient_writes_exactly_its_output(weo, dims):
     assert not bool(sentinel_mask(out).any())
     check_guards(buf, out.numel())
     op.close()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 2, 6), (8, 2, 2, 2), (16, 6, 2, 4)])
+@pytest.mark.parametrize("mode,nrhs", [(1, 1), (2, 3)])
+def test_staged_hop_writes_exactly_its_output(weo, dims, mode, nrhs):
+    """The TMA-staged hop (tiles of 8, 8 and 48 sites; one right-hand side, and
+    the multi-RHS kernel): M_eo, M_eo^dag and single hops of both parities."""
+    import torch
+
+    U = gen.gauge_field(dims, "haar", seed=153)
+    psi = gen.gaussian_spinor(dims, nrhs=nrhs, seed=154)
+    op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
+    weo.wilson_eo_set_staging(op.handle, mode)
+    x = to_device(to_planar(psi), "f32")
+    if nrhs == 1:
+        x = x[0]
+    x0 = x.clone()
+    calls = [lambda y: weo.wilson_eo_apply(op.handle, y, x, nrhs),
+             lambda y: weo.wilson_eo_apply_dag(op.handle, y, x, nrhs)]
+    for par in (0, 1):
+        calls.append(lambda y, par=par: weo.wilson_eo_hop(op.handle, par, False, y, x, nrhs))
+    for call in calls:
+        buf, y = guarded(tuple(x.shape), torch.complex64)
+        call(y)
+        weo.wilson_eo_check(op.handle)
+        torch.cuda.synchronize()
+        assert not bool(sentinel_mask(y).any()), "output element not written"
+        check_guards(buf, y.numel())
+        assert torch.equal(x, x0), "input modified"
+    op.close()
