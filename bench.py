@@ -83,6 +83,20 @@ def staged_main(args):
     return args.staged and args.prec == "f32" and args.linkfmt == 18 and not args.ff and not args.algo
 
 
+def workload_config(args, world):
+    """The workload both arms measure (the same dict in both JSON lines)."""
+    link_bytes = 144 if args.ff else {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}[args.prec]
+    if args.linkfmt == 12 and not args.ff:
+        link_bytes = link_bytes * 2 // 3
+    links_mb = 4 * int(np.prod(DIMS)) * link_bytes / 1e6
+    return {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
+            "links": f"exp(i*{EPS}*H), {18 if args.ff else args.linkfmt}-real", "prec": args.prec,
+            "flop_per_site_per_meo": FLOP_PER_SITE,
+            "l2": f"inputs larger than L2 ({links_mb:.0f} MB of links per hop pass)"
+                  if links_mb > 129 else f"links {links_mb:.0f} MB per hop pass (L2 129 MB)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def workload_name(args):
     prec = "float-float (FP64-class)" if args.ff else {"f64": "FP64", "f32": "FP32", "f16": "FP16 storage",
                                                         "bf16": "BF16 storage"}[args.prec]
@@ -277,6 +291,7 @@ def run_ours(args, rank, world, local):
 
     configure(op)
     stream = torch.cuda.current_stream(dev)
+    staged_mb = None
 
     def step():
         if args.ff:
@@ -292,9 +307,15 @@ def run_ours(args, rank, world, local):
 
             dist.barrier()
 
+    free0 = torch.cuda.mem_get_info(dev)[0]
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    if staged_main(args):
+        # the staged hop's per-tile link blocks (2 x 576 B per even site), built
+        # on first use: device memory they took beside the packed links
+        staged_mb = round((free0 - torch.cuda.mem_get_info(dev)[0]) / 1e6, 1)
+    device_mb = round(weo.wilson_eo_info(op.handle).get("device_bytes", 0) / 1e6, 1)
 
     # ---- timed region: device events on the launching stream
     weo.wilson_eo_profile(op.handle, True)
@@ -521,15 +542,14 @@ def run_ours(args, rank, world, local):
                      {"f32": "f32", "f64": "f64", "f16": "f16-storage/f32",
                       "bf16": "bf16-storage/f32"}[args.prec],
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
-                       "links": f"exp(i*{EPS}*H), {args.linkfmt}-real", "prec": args.prec,
-                       "flop_per_site_per_meo": FLOP_PER_SITE,
-                       "algo": "fused" if args.algo else
-                               "two staged (TMA) hop launches" if staged_main(args) else "two hop launches",
-                       "threads": args.threads, "second_hop_order": "down" if args.order else "up",
-                       "l2": f"inputs larger than L2 ({links_mb:.0f} MB of links per hop pass)"
-                             if links_mb > 129 else f"links {links_mb:.0f} MB per hop pass (L2 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args, world),
+            "impl_config": {"algo": "fused" if args.algo else
+                                    "two staged (TMA) hop launches" if staged_main(args)
+                                    else "two hop launches",
+                            "threads": args.threads,
+                            "second_hop_order": "down" if args.order else "up",
+                            "staged_link_blocks_mb": staged_mb,
+                            "device_mb": device_mb},
             "gflops_1368_per_site": round(value * 1368 / FLOP_PER_SITE, 1),
             "site_updates_per_s": round(world * 2 * V / (ms_step * 1e-3), 0),
             "roofline": roofline, "hop_gflops": hops, "cpu_baseline": cpu, "e2e": e2e,
@@ -682,6 +702,12 @@ def multi_solve_comparison(U, dev):
                          "reliable_updates": info["reliable_updates"],
                          "max_true_relres": max(info["true_relres"]), "converged": info["converged"],
                          "tuned": cfg}
+            if name == "mixed_f16" and info["converged"]:
+                # every system's residual recomputed by the FP64 oracle (not timed)
+                xh = np.moveaxis(x.cpu().numpy(), -1, -3)
+                bh = np.moveaxis(b.cpu().numpy(), -1, -3)
+                res[name]["oracle_max_true_relres"] = max(
+                    oracle_relres(U, KAPPA, xh[r], bh[r], DIMS) for r in range(12))
             del x
         except weo.WilsonEOError as exc:
             res[name] = {"error": str(exc)}
@@ -690,6 +716,22 @@ def multi_solve_comparison(U, dev):
     if res["plain_f64"].get("converged") and res["mixed_f16"].get("converged"):
         res["speedup_f16_vs_plain_f64"] = round(res["plain_f64"]["seconds"] / res["mixed_f16"]["seconds"], 2)
     return res
+
+
+# solves of the default run (the others are selectable with --solve-variants)
+DEFAULT_SOLVES = ("mixed_f16_fused", "mixed_bf16_fused", "mixed_f32_fused", "mixed_f16_two_pass",
+                  "mixed_f16_l12_two_pass", "mixed_f16_l12_tuned", "plain_f64")
+
+
+def oracle_relres(U, kappa, x, b, dims):
+    """|b - M^dag M x| / |b| recomputed by the FP64 oracle on all host cores
+    (x, b in the oracle's (V/2, 4, 3) layout). A check of the GPU's answer,
+    run outside every timed region."""
+    import oracle
+
+    oracle.set_threads(os.cpu_count() or 1)
+    ax = oracle.meo_dag(U, kappa, oracle.meo(U, kappa, x, dims), dims)
+    return float(np.linalg.norm(b - ax) / np.linalg.norm(b))
 
 
 def solve_comparison(dev, dims, only=None):
@@ -705,9 +747,7 @@ def solve_comparison(dev, dims, only=None):
     b = gen.gaussian_spinor(dims, seed=1)[0]
     gen_s = time.perf_counter() - t0
     Ud = torch.from_numpy(U).to(dev)
-    del U
     bd = torch.from_numpy(np.ascontiguousarray(np.moveaxis(b, 0, -1))).to(dev)
-    del b
     res = {"lattice": list(dims), "kappa": 0.135, "tol": 1e-10, "field_gen_s": round(gen_s, 1),
            "note": "fused: inner M_eo in one persistent launch (first hop 4 t-slices ahead); "
                    "two_pass: two hop launches; both keep the odd intermediate in 16-bit "
@@ -724,7 +764,7 @@ def solve_comparison(dev, dims, only=None):
                                     ("mixed_f16_l12_tuned", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0),
                                     ("plain_f64_tuned", "f64", False, 0)):
-        if only and name not in only:
+        if (only and name not in only) or (not only and name not in DEFAULT_SOLVES):
             continue
         op = weo.WilsonEO(dims, 0.135, Ud, prec=prec, linkfmt=12 if "_l12" in name else 18)
         if algo:
@@ -741,6 +781,10 @@ def solve_comparison(dev, dims, only=None):
             x, info = op.solve(bd, tol=1e-10, maxiter=20000, mixed=mixed)
             res[name] = {k: (round(v, 4) if isinstance(v, float) and k == "seconds" else v)
                          for k, v in info.items()}
+            if info["converged"]:
+                # the oracle's own FP64 residual of the returned x (after the timing)
+                res[name]["oracle_true_relres"] = oracle_relres(
+                    U, 0.135, np.moveaxis(x.cpu().numpy(), -1, 0), b, dims)
             del x
         except weo.WilsonEOError as exc:
             res[name] = {"error": str(exc)}
@@ -849,8 +893,7 @@ def run_reference(args, rank, world, local):
            "n_gpus": world, "steps": args.steps, "warmup": max(1, args.warmup),
            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args), "lattice": list(DIMS), "kappa": KAPPA,
-                      "sample_lattice": list(sd)},
+           "config": workload_config(args, world), "sample_lattice": list(sd),
            "cpu_baseline": {"value": round(value, 3), "unit": "GFlop/s",
                             "cores": oracle.get_threads(), "kind": "oracle", "sample": sample,
                             "cpu_model": cpu_model()},

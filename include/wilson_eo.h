@@ -405,12 +405,16 @@ int wilson_eo_profile_read(wilson_eo_t h, int max_kernels, char *names, int name
  *   gauge  canonical gauge field, complex64, device memory
  *   in_e   one canonical FP32 even spinor (planar complex64), device memory
  *   out_e  receives the result; must not alias in_e
- * Host arrays are rejected with WEO_ERR_ARG (staging them would allocate).
+ * All three arrays must be memory of the current device (or managed memory);
+ * host arrays (staging them would allocate) and arrays of another GPU are
+ * rejected with WEO_ERR_ARG before anything is launched.
  * The odd-site intermediate H_oe in_e lives in a fixed 32 MiB array compiled
  * into the library (a file-scope __device__ variable), which every GPU that
  * loads the library holds until the process exits. The first call on a device
- * looks up that array's device address for the current device; make that first
- * call before any stream capture. All calls share the array and it keeps the
+ * looks up that array's device address for the current device and keeps it;
+ * make that first call before any stream capture. The kept address dies with
+ * the device's context: do not call this entry point on a device after
+ * cudaDeviceReset of that device in the same process. All calls share the array and it keeps the
  * last call's contents; nothing in it has to start at zero because each call
  * writes every entry before reading it. Calls that overlap on the GPU (streams
  * without ordering between them, or several host threads) race on the array:

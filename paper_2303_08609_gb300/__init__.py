@@ -294,9 +294,28 @@ def wilson_eo_force(h, force, dS_dphi_e, phi_e, stream=None):
            "wilson_eo_force")
 
 
+def _noalloc_device(arrays):
+    """CUDA device index shared by the torch tensors among ``arrays`` (None if
+    there are none). Tensors that are not on a CUDA device, or on different
+    devices, are refused here, before the library is called."""
+    devs = set()
+    for a in arrays:
+        if not hasattr(a, "data_ptr") or not hasattr(a, "is_cuda"):
+            continue  # numpy arrays and raw pointers: the library checks those
+        d = a.device
+        if d.type != "cuda":
+            raise ValueError(f"wilson_eo_apply_noalloc takes CUDA device arrays only, got {d}")
+        devs.add(d.index)
+    if len(devs) > 1:
+        raise ValueError(f"wilson_eo_apply_noalloc: arrays on different devices {sorted(devs)}")
+    return devs.pop() if devs else None
+
+
 def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=None):
     """FP32 M_eo (or M_eo^dag) on caller-owned device arrays; the library
-    allocates nothing for it (see the header for the scratch-array rules)."""
+    allocates nothing for it (see the header for the scratch-array rules).
+    The call runs with the arrays' device current."""
+    dev = _noalloc_device((gauge, out_e, in_e))
     V = int(np.prod([int(x) for x in dims]))
     for a, need, what in ((gauge, 4 * V * 9 * 8, "gauge"), (out_e, 6 * V * 8, "out_e"),
                           (in_e, 6 * V * 8, "in_e")):
@@ -308,9 +327,19 @@ def wilson_eo_apply_noalloc(dims, kappa, gauge, out_e, in_e, dag=False, stream=N
         if nb is not None and nb < need and valid_dims and V // 2 <= 349525:
             raise ValueError(f"wilson_eo_apply_noalloc: {what} has {nb} bytes, needs {need}")
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
-    _check(_load().wilson_eo_apply_noalloc(d, float(kappa), _ptr(gauge), _ptr(out_e), _ptr(in_e),
-                                           int(bool(dag)), _stream(stream)),
-           "wilson_eo_apply_noalloc")
+
+    def call():
+        return _load().wilson_eo_apply_noalloc(d, float(kappa), _ptr(gauge), _ptr(out_e),
+                                               _ptr(in_e), int(bool(dag)), _stream(stream))
+
+    if dev is None:
+        st = call()
+    else:
+        import torch
+
+        with torch.cuda.device(dev):
+            st = call()
+    _check(st, "wilson_eo_apply_noalloc")
 
 
 def wilson_eo_set_rhs_lanes(h, lanes):

@@ -14,7 +14,10 @@
 // Its host-side name is only a stand-in; host code must not pass it to a
 // kernel. The device address is looked up with cudaGetSymbolAddress once per
 // device (the first call of the entry point on that device does it) and that
-// address is what the kernels receive.
+// address is what the kernels receive. The cached address belongs to the
+// device's current primary context: after cudaDeviceReset (or any other end of
+// that context) it is stale, so the entry point must not be called on a device
+// once that device has been reset in this process.
 #include <mutex>
 
 #include "weo_internal.h"
@@ -47,13 +50,15 @@ static int scratch_address(int device, void **addr)
 }
 
 // Canonical complex64 link U_mu at lexicographic site lex: 9 complex, row-major.
+// Each link is read by two sites of a hop and again by the other hop: plain
+// cached loads, so the repeat reads can hit in L2.
 __device__ __forceinline__ void load_canonical_link(const float2 *gauge, long long V, int mu,
                                                     long long lex, cx<float> U[3][3])
 {
     const float2 *p = gauge + 9 * (mu * V + lex);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        float2 v = __ldcs(p + k);
+        float2 v = __ldg(p + k);
         U[k / 3][k % 3] = {v.x, v.y};
     }
 }
@@ -145,14 +150,17 @@ __global__ void __launch_bounds__(128) noalloc_hop_kernel(int lxh, int ly, int l
     SpF32::store(out, vh, i, acc);
 }
 
-static bool device_accessible(const void *p)
+// Device memory of `device` itself, or managed memory. Device memory of another
+// GPU is refused: without peer access the kernels would fault on it.
+static bool device_accessible(const void *p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace weo
@@ -176,10 +184,12 @@ extern "C" int wilson_eo_apply_noalloc(const int dims[4], double kappa, const vo
             return set_error(WEO_ERR_DIMS,
                              "lattice too large for wilson_eo_apply_noalloc: V/2 must be <= 349525 "
                              "sites (its fixed scratch holds one FP32 odd-site spinor, 32 MiB)");
-        if (!device_accessible(gauge) || !device_accessible(out_e) || !device_accessible(in_e))
-            return set_error(WEO_ERR_ARG, "wilson_eo_apply_noalloc takes device arrays only");
         int device = 0;
         WEO_CUDA(cudaGetDevice(&device));
+        if (!device_accessible(gauge, device) || !device_accessible(out_e, device) ||
+            !device_accessible(in_e, device))
+            return set_error(WEO_ERR_ARG,
+                             "wilson_eo_apply_noalloc takes device arrays of the current device only");
         void *scratch = nullptr;
         WEO_TRY(scratch_address(device, &scratch));
         cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -40,3 +40,15 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def fields_32x64():
+    """The benchmark workload's inputs, generated once per session:
+    32^3 x 64, exp(i 0.4 H) links (seed 0), Gaussian even source (seed 0)."""
+    import gen
+
+    dims = (32, 32, 32, 64)
+    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    psi = gen.gaussian_spinor(dims, seed=0)[0]
+    return dims, U, psi

@@ -122,3 +122,31 @@ def test_staging_rejects_null_and_bad_values(lib):
     assert lib.wilson_eo_set_staging(None, 1, 0, 0) == -1
     assert lib.wilson_eo_get_staging(None, None, None, None) == -1
     assert lib.wilson_eo_inject_staged_timeout(None, None, None, None) == -1
+
+
+def test_noalloc_refuses_tensors_off_the_gpu_before_the_library(lib):
+    """Torch tensors that are not CUDA arrays (here on the meta and CPU devices)
+    are refused by the binding before any library call, as are arrays on
+    different GPUs."""
+    import torch
+
+    import paper_2303_08609_gb300 as weo
+
+    for device in ("meta", "cpu"):
+        z = torch.empty(8, dtype=torch.complex64, device=device)
+        with pytest.raises(ValueError, match="CUDA device arrays only"):
+            weo.wilson_eo_apply_noalloc((4, 4, 4, 4), 0.1, z, z.clone(), z)
+    assert weo._noalloc_device((np.zeros(2), None, 5)) is None
+
+    class OnGpu:  # stands in for a CUDA tensor: only its device is looked at
+        is_cuda = True
+
+        def __init__(self, index):
+            self.device = torch.device("cuda", index)
+
+        def data_ptr(self):
+            return 0
+
+    assert weo._noalloc_device((OnGpu(1), OnGpu(1), None)) == 1
+    with pytest.raises(ValueError, match="different devices"):
+        weo.wilson_eo_apply_noalloc((4, 4, 4, 4), 0.1, OnGpu(0), OnGpu(1), OnGpu(0))

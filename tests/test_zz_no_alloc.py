@@ -13,9 +13,11 @@ import numpy as np
 import pytest
 
 import gen
-from gpu_util import TOL, rel_l2, to_planar
+from gpu_util import TOL, from_planar, rel_l2, to_planar
 
 pytestmark = pytest.mark.gpu
+
+GUARD = 4096  # complex elements of NaN sentinel before and after each output
 
 
 @pytest.fixture(scope="module")
@@ -79,3 +81,32 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(weo):
     with pytest.raises(weo.WilsonEOError) as e:
         weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, Uh, torch.empty_like(xd), xd)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 6, 4, 10), (6, 4, 2, 6), (8, 6, 4, 6)])
+def test_noalloc_ragged_lattices_match_oracle_and_write_only_the_output(weo, oracle_lib, dims):
+    """Extents of 2, Lx = 2 and V/2 not a multiple of the 128-thread block (the
+    kernels' tail guard): the result equals the FP64 oracle's, every output
+    element is written, nothing before or after the output is, and the inputs
+    are unchanged."""
+    import torch
+
+    U = gen.gauge_field(dims, "haar", seed=64)
+    psi = gen.gaussian_spinor(dims, seed=65)[0]
+    Ud = torch.from_numpy(U.astype(np.complex64)).cuda()
+    x = torch.from_numpy(to_planar(psi).astype(np.complex64)).cuda()
+    U0, x0 = Ud.clone(), x.clone()
+    n = x.numel()
+    for dag in (False, True):
+        buf = torch.full((n + 2 * GUARD,), complex(float("nan"), 7.0), dtype=torch.complex64,
+                         device="cuda")
+        y = buf[GUARD:GUARD + n].view(x.shape)
+        weo.wilson_eo_apply_noalloc(dims, 0.13, Ud, y, x, dag=dag)
+        torch.cuda.synchronize()
+        sentinel = torch.isnan(buf.real) & (buf.imag == 7.0)
+        assert not bool(sentinel[GUARD:GUARD + n].any()), "output element not written"
+        assert bool(sentinel[:GUARD].all()) and bool(sentinel[GUARD + n:].all()), \
+            "write outside the output"
+        assert torch.equal(x, x0) and torch.equal(Ud, U0), "input modified"
+        want = (oracle_lib.meo_dag if dag else oracle_lib.meo)(U, 0.13, psi, dims)
+        assert rel_l2(from_planar(y.cpu().numpy()), want) <= TOL["f32"]
