@@ -4,7 +4,8 @@
 // walks the tiles of every lattice's first hop, synchronises once across the
 // grid, then walks the tiles of every second hop (with the axpy of Eq. 4). A
 // tile is CTA-sized in sites and covers R right-hand sides, which share each
-// link load. Lattices need not fill the GPU on their own: small and large
+// link load; the tiles of one site block follow each other, so the other
+// right-hand-side blocks find its links in L2. Lattices need not fill the GPU on their own: small and large
 // lattices share one launch.
 #include <cooperative_groups.h>
 
@@ -41,16 +42,19 @@ __global__ void __launch_bounds__(kBatchThreads) batch_meo_kernel(const __grid_c
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int k = find_lattice(a, tile);
         const long long local = tile - a.tile_begin[k];
-        const int rb = (int)(local / a.site_tiles[k]);
-        const long long site = (local - (long long)rb * a.site_tiles[k]) * kBatchThreads + threadIdx.x;
+        // right-hand-side block fastest: the tiles sharing links run side by side
+        const int nrb = (a.first[k].nrhs + R - 1) / R;
+        const int rb = (int)(local % nrb);
+        const long long site = (local / nrb) * kBatchThreads + threadIdx.x;
         if (site < a.first[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, false, R>(a.first[k], (int)site, rb * R);
     }
     cg::this_grid().sync();
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
         const int k = find_lattice(a, tile);
         const long long local = tile - a.tile_begin[k];
-        const int rb = (int)(local / a.site_tiles[k]);
-        const long long site = (local - (long long)rb * a.site_tiles[k]) * kBatchThreads + threadIdx.x;
+        const int nrb = (a.second[k].nrhs + R - 1) / R;
+        const int rb = (int)(local % nrb);
+        const long long site = (local / nrb) * kBatchThreads + threadIdx.x;
         if (site < a.second[k].vh) hop_site<Sp, Sp, Sp, Lk, Dag, true, R>(a.second[k], (int)site, rb * R);
     }
 }

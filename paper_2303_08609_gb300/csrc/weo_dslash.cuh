@@ -206,16 +206,30 @@ __device__ __forceinline__ void hop_site(const HopParams &p, const int i, const 
     }
 }
 
-// One output site per thread. With p.reverse the CTAs cover the sites from the
-// top down, so a hop that follows another one first reads the part of its input
-// that was written last (and is still in L2).
+// Block order of the hop kernels: a 1-D grid of (site block, right-hand-side
+// block) pairs with the right-hand-side block varying fastest, so the CTAs of
+// one site block -- which read the same links -- run side by side and every
+// link comes from HBM once per hop, the other right-hand-side blocks finding it
+// in L2. With p.reverse the site blocks are taken from the top down, so a hop
+// that follows another one first reads the part of its input that was written
+// last (and is still in L2). nrb = right-hand-side blocks.
+__device__ __forceinline__ void block_coords(const HopParams &p, int nrb, int &site_block, int &rhs_block)
+{
+    const int nsb = (int)gridDim.x / nrb;
+    rhs_block = (int)blockIdx.x % nrb;
+    const int sb = (int)blockIdx.x / nrb;
+    site_block = p.reverse ? nsb - 1 - sb : sb;
+}
+
+// One output site per thread.
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 __global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
 {
-    const int b = p.reverse ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    int b, rb;
+    block_coords(p, (p.nrhs + R - 1) / R, b, rb);
     const int i = b * blockDim.x + threadIdx.x;
     if (i >= p.vh) return;
-    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, blockIdx.y * R);
+    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, rb * R);
 }
 
 // The same kernel with the register allocation capped at 64 (four CTAs of 256
@@ -226,10 +240,11 @@ __global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 __global__ void __launch_bounds__(256, 4) hop_kernel_occ(const HopParams p)
 {
-    const int b = p.reverse ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    int b, rb;
+    block_coords(p, (p.nrhs + R - 1) / R, b, rb);
     const int i = b * blockDim.x + threadIdx.x;
     if (i >= p.vh) return;
-    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, blockIdx.y * R);
+    hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, rb * R);
 }
 
 // Right-hand sides on neighbouring lanes: NL consecutive threads take one site
@@ -239,9 +254,10 @@ __global__ void __launch_bounds__(256, 4) hop_kernel_occ(const HopParams p)
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NL>
 __global__ void __launch_bounds__(256, 4) hop_kernel_lanes(const HopParams p)
 {
-    const int b = p.reverse ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    int b, rb;
+    block_coords(p, (p.nrhs + NL - 1) / NL, b, rb);
     const int i = b * (int)(blockDim.x / NL) + (int)threadIdx.x / NL;
-    const int r = (int)blockIdx.y * NL + (int)threadIdx.x % NL;
+    const int r = rb * NL + (int)threadIdx.x % NL;
     if (i >= p.vh || r >= p.nrhs) return;
     hop_site<SIn, SOut, SX, Lk, Dag, Axpy, 1>(p, i, r);
 }

@@ -12,7 +12,8 @@ template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NL
 int launch_lanes(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
     const int sites = cfg.threads / NL;
-    dim3 grid((unsigned)((p.vh + sites - 1) / sites), (unsigned)((p.nrhs + NL - 1) / NL));
+    // (site block, right-hand-side block) pairs, right-hand-side block fastest
+    dim3 grid((unsigned)(((p.vh + sites - 1) / sites) * ((p.nrhs + NL - 1) / NL)));
     hop_kernel_lanes<SIn, SOut, SX, Lk, Dag, Axpy, NL><<<grid, cfg.threads, 0, s>>>(p);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
@@ -31,7 +32,7 @@ int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
         if (nl == 2) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 2>(p, cfg, s);
     }
     const int threads = cfg.threads;
-    dim3 grid((unsigned)((p.vh + threads - 1) / threads), (unsigned)((p.nrhs + R - 1) / R));
+    dim3 grid((unsigned)(((p.vh + threads - 1) / threads) * ((p.nrhs + R - 1) / R)));
     // the 64-register cap pays for 18-real FP32 and 16-bit links; the FP32
     // 12-real rebuild spills too much under it
     if constexpr (sizeof(typename SOut::real) == 4 && R == 1 && !std::is_same<Lk, LkF32_12>::value)

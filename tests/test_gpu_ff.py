@@ -57,12 +57,12 @@ def test_ff_host_arrays_and_set_gauge(weo, oracle_lib):
     op.close()
 
 
-def test_ff_full_size_sampled(weo, oracle_lib):
+def test_ff_full_size_sampled(weo, oracle_lib, fields_32x64):
     import torch
 
     dims = (32, 32, 32, 64)
     vh = int(np.prod(dims)) // 2
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    dims, U, _ = fields_32x64  # smooth links, seed 0
     psi = gen.gaussian_spinor(dims, seed=0)[0]
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f64")
     x = to_device(to_planar(psi), "f64")

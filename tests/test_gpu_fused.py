@@ -64,13 +64,13 @@ def test_fused_link_formats(weo, oracle_lib, prec, fmt):
     op.close()
 
 
-def test_fused_full_size_sampled_and_solver(weo, oracle_lib):
+def test_fused_full_size_sampled_and_solver(weo, oracle_lib, fields_32x64):
     """32^3 x 64 sampled sites, then a mixed solve whose inner operator is fused."""
     import torch
 
     dims = (32, 32, 32, 64)
     vh = int(np.prod(dims)) // 2
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    dims, U, _ = fields_32x64  # smooth links, seed 0
     psi = gen.gaussian_spinor(dims, seed=0)[0]
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
     weo.wilson_eo_set_algorithm(op.handle, "fused", 8, 128)

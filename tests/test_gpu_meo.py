@@ -71,14 +71,14 @@ def test_meo_ragged_and_degenerate_dims(weo, oracle_lib, dims, prec):
 
 @pytest.mark.parametrize("prec,fmt", [("f64", 18), ("f32", 18), ("f32", 12), ("f16", 12),
                                       ("bf16", 18)])
-def test_meo_full_size_sampled(weo, oracle_lib, prec, fmt):
+def test_meo_full_size_sampled(weo, oracle_lib, prec, fmt, fields_32x64):
     """32^3 x 64, kappa = 0.13, exp(i 0.4 H) links: 400 sampled output sites
     against the oracle's per-site evaluation, plus global properties."""
     import torch
 
     dims = (32, 32, 32, 64)
     vh = 32 * 32 * 32 * 64 // 2
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    dims, U, _ = fields_32x64  # smooth links, seed 0
     psi = gen.gaussian_spinor(dims, seed=0)[0]
     op = weo.WilsonEO(dims, 0.13, to_device(U, "f64"), prec=prec, linkfmt=fmt)
     x = torch.from_numpy(to_planar(psi).astype(np_dtype(prec))).cuda()

@@ -63,13 +63,13 @@ def test_staged_meo_matches_oracle(weo, oracle_lib, dims, order):
     op.close()
 
 
-def test_staged_full_size_sampled(weo, oracle_lib):
+def test_staged_full_size_sampled(weo, oracle_lib, fields_32x64):
     """32^3 x 64 (tiles of 4 rows = 64 sites, 16384 tiles over 152 CTAs)."""
     import torch
 
     dims = (32, 32, 32, 64)
     vh = int(np.prod(dims)) // 2
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    dims, U, _ = fields_32x64  # smooth links, seed 0
     psi = gen.gaussian_spinor(dims, seed=0)[0]
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
     x = to_device(to_planar(psi), "f32")
@@ -273,14 +273,14 @@ def test_staged_multi_rhs_matches_oracle(weo, oracle_lib, dims, nrhs):
     op.close()
 
 
-def test_staged_multi_rhs_full_size_sampled(weo, oracle_lib):
+def test_staged_multi_rhs_full_size_sampled(weo, oracle_lib, fields_32x64):
     """32^3 x 64 with 12 point-source-like right-hand sides (Gaussian here),
     sampled sites of every right-hand side against the oracle."""
     import torch
 
     dims = (32, 32, 32, 64)
     vh = int(np.prod(dims)) // 2
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
+    dims, U, _ = fields_32x64  # smooth links, seed 0
     psi = gen.gaussian_spinor(dims, nrhs=12, seed=320)
     op = weo.WilsonEO(dims, 0.13, to_device(U), prec="f32")
     weo.wilson_eo_set_staging(op.handle, 2)

@@ -76,11 +76,15 @@ def test_noalloc_rejects_lattices_beyond_its_scratch(weo):
     assert e.value.status == -2
     assert "349525" in weo.wilson_eo_last_error()
     # host arrays are refused by the library itself (staging them would allocate)
-    Uh = torch.zeros((4, 8**4, 3, 3), dtype=torch.complex64)
+    Uh = np.zeros((4, 8**4, 3, 3), dtype=np.complex64)
     xd = torch.zeros((4, 3, 8**4 // 2), dtype=torch.complex64, device="cuda")
     with pytest.raises(weo.WilsonEOError) as e:
         weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, Uh, torch.empty_like(xd), xd)
     assert e.value.status == -1
+    # a host tensor beside device tensors is refused by the binding, before the library
+    with pytest.raises(ValueError):
+        weo.wilson_eo_apply_noalloc((8, 8, 8, 8), 0.1, torch.from_numpy(Uh),
+                                    torch.empty_like(xd), xd)
 
 
 @pytest.mark.parametrize("dims", [(2, 2, 2, 2), (2, 6, 4, 10), (6, 4, 2, 6), (8, 6, 4, 6)])
