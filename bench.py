@@ -423,8 +423,14 @@ def run_ours(args, rank, world, local):
     ns = min(range(2, NS_E2E + 1), key=lambda k: e2e_ms[k])
     e2e = {"value": round(world * flops_step / (e2e_ms[ns] * 1e-3) / 1e9, 1), "unit": "GFlop/s",
            "ms_per_step": round(e2e_ms[ns], 4), "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
-           "streams": ns, "ms_per_step_by_streams": {k: round(v, 4) for k, v in e2e_ms.items()},
+           "mode": f"pipelined: {ns} handles on {ns} streams take the steps in turn, each "
+                   f"holding its own packed links (and staged link blocks)",
+           "streams": ns, "handles": ns,
+           "ms_per_step_by_streams": {k: round(v, 4) for k, v in e2e_ms.items()},
            "one_stream_value": round(world * flops_step / (e2e_ms[1] * 1e-3) / 1e9, 1),
+           "per_call_latency_ms": round(e2e_ms[1], 4),
+           "per_call_note": "one handle, one stream: host->device copy, M_eo, M_eo^dag and the "
+                            "device->host copy of one step back to back (the ABI's latency per step)",
            "result_finite": bool(np.isfinite(zres).all())}
     for o_ in ops2[1:]:
         o_.close()
@@ -477,6 +483,9 @@ def run_ours(args, rank, world, local):
             lab, (km, kc) = max(vp.items(), key=lambda kv: kv[1][0])
             ab = algo_bytes_per_site(lab)
             ent = {"gflops": round(flops_step / (vms * 1e-3) / 1e9, 1),
+                   "hop_gflops": {k: round((1368 if "_axpy" in k else 1320) * (V // 2)
+                                           / (ms_ / cnt_ * 1e-3) / 1e9, 1)
+                                  for k, (ms_, cnt_) in vp.items()},
                    "ms_per_step": round(vms, 4), "dominant_kernel": lab,
                    "kernel_gbs": round(ab * V / (km / kc * 1e-3) / 1e9, 1) if ab else None,
                    "useful_work_frac": round(2 * useful_bytes_per_site(prec, fmt) * V
@@ -491,6 +500,33 @@ def run_ours(args, rank, world, local):
             variants[f"{prec}_l{fmt}" + ("", "_fused", "_staged")[algo]] = ent
             o2.close()
             del xv, yv, zv
+        # the same step on fully Haar-random links (seed 0): FP32 18-real staged
+        # and two-launch, FP64 18-real
+        import gen
+
+        Uh = torch.from_numpy(gen.gauge_field(DIMS, "haar", seed=0)).to(dev)
+        for prec, algo in (("f32", 2), ("f32", 0), ("f64", 0)):
+            o2 = weo.WilsonEO(DIMS, KAPPA, Uh, prec=prec, linkfmt=18)
+            if algo == 2:
+                weo.wilson_eo_set_staging(o2.handle, True)
+            xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev) \
+                if prec == "f64" else x
+            yv, zv = torch.empty_like(xv), torch.empty_like(xv)
+            n = 20 if prec == "f64" else 200
+            weo.wilson_eo_profile(o2.handle, True)
+            vms = timed(lambda: (weo.wilson_eo_apply(o2.handle, yv, xv, 1, stream),
+                                 weo.wilson_eo_apply_dag(o2.handle, zv, yv, 1, stream)), n, stream)
+            weo.wilson_eo_check(o2.handle, stream)
+            vp = weo.wilson_eo_profile_read(o2.handle, reset=True)
+            variants[f"{prec}_l18" + ("", "", "_staged")[algo] + "_haar"] = {
+                "gflops": round(flops_step / (vms * 1e-3) / 1e9, 1), "ms_per_step": round(vms, 4),
+                "hop_gflops": {k: round((1368 if "_axpy" in k else 1320) * (V // 2)
+                                        / (ms_ / cnt_ * 1e-3) / 1e9, 1)
+                               for k, (ms_, cnt_) in vp.items()},
+                "links": "Haar-random SU(3), seed 0"}
+            o2.close()
+            del xv, yv, zv
+        del Uh
         # float-float M_eo (FP64-class accuracy on the FP32 pipes) on complex128 spinors
         o2 = weo.WilsonEO(DIMS, KAPPA, Ud, prec="f64")
         xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev)
@@ -530,6 +566,7 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(U, psi)
+        cpu["small_workloads"] = oracle_plan()
 
     if rank == 0:
         import oracle  # noqa: F401  (only for the baseline / check above)
@@ -623,9 +660,28 @@ def extras(U, psi, dev, stream):
         res[f"rhs_per_thread_{rb}"] = {"ms_per_step": round(ms, 4),
                                        "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
     t, rb, tms = weo.wilson_eo_tune(op.handle, 12, stream)
-    res["tuned"] = {"threads": t, "rhs_per_thread": rb, "ms_per_meo": round(tms, 4),
-                    "gflops": round(12 * FLOP_PER_SITE * V / (tms * 1e-3) / 1e9, 1)}
+    lanes = weo.wilson_eo_get_launch(op.handle)[2]
+    res["tuned"] = {"threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes, "ms_per_meo": round(tms, 4),
+                    "gflops": round(12 * FLOP_PER_SITE * V / (tms * 1e-3) / 1e9, 1),
+                    "two_pass_model_bytes": int((576 + 240 * 12) * V),
+                    "two_pass_model_frac": round((576 + 240 * 12) * V / (tms * 1e-3) / 1e9
+                                                 / measured_peaks()[0], 4)}
     out["multi_rhs_12_point_sources_f32"] = res
+    del x, y, z
+    # 16 right-hand sides: the 12 point sources and 4 Gaussian vectors (seed 9)
+    g4 = np.moveaxis(gen.gaussian_spinor(DIMS, nrhs=4, seed=9), 1, -1).astype(np.complex64)
+    x = torch.from_numpy(np.concatenate([src, g4])).to(dev)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    t, rb, tms = weo.wilson_eo_tune(op.handle, 16, stream)
+    lanes = weo.wilson_eo_get_launch(op.handle)[2]
+    ms = timed(lambda: (weo.wilson_eo_apply(op.handle, y, x, 16, stream),
+                        weo.wilson_eo_apply_dag(op.handle, z, y, 16, stream)), 20, stream)
+    out["multi_rhs_16_f32"] = {"rhs": "12 spin-colour point sources + 4 Gaussian (seed 9)",
+                               "threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
+                               "ms_per_step": round(ms, 4),
+                               "gflops": round(16 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1),
+                               "two_pass_model_frac": round(2 * (576 + 240 * 16) * V / (ms * 1e-3) / 1e9
+                                                            / measured_peaks()[0], 4)}
     del x, y, z
     # force: chi = M phi forward, backward M^dag g + link gradient (FP32)
     from paper_2303_08609_gb300.autograd import pseudofermion_action
@@ -762,6 +818,11 @@ def solve_comparison(dev, dims, only=None):
                                     ("mixed_f16_two_pass_fp64res", "f16", True, 0),
                                     ("mixed_f16_two_pass_delta0.03", "f16", True, 0),
                                     ("mixed_f16_l12_tuned", "f16", True, 0),
+                                    ("mixed_bf16_two_pass", "bf16", True, 0),
+                                    ("mixed_bf16_l12_two_pass", "bf16", True, 0),
+                                    ("mixed_bf16_restart", "bf16", True, 0),
+                                    ("mixed_bf16_l12_restart", "bf16", True, 0),
+                                    ("mixed_f16_l12_restart", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0),
                                     ("plain_f64_tuned", "f64", False, 0)):
         if (only and name not in only) or (not only and name not in DEFAULT_SOLVES):
@@ -773,6 +834,8 @@ def solve_comparison(dev, dims, only=None):
             weo.wilson_eo_solver_config(op.handle, delta=float(name.split("delta")[1]))
         if name.endswith("fp64res"):
             weo.wilson_eo_solver_residual(op.handle, 0)
+        if "restart" in name:  # defect correction: new direction at every reliable update
+            weo.wilson_eo_solver_restart(op.handle, 1)
         if name.endswith("_tuned"):  # autotuned operator (tuning not timed)
             weo.wilson_eo_tune(op.handle, nrhs=1)
             res.setdefault("tuned", {})[name] = {**weo.wilson_eo_get_algorithm(op.handle),
@@ -856,6 +919,49 @@ def cpu_baseline(U, psi, reps=3):
                               "sample": f"one step on the first {sd[3]} time slices "
                                         f"({'x'.join(map(str, sd))}, periodic), {dt1:.2f} s"},
             "cpu_model": cpu_model()}
+
+
+def oracle_plan(budget_s=40.0):
+    """The FP64 oracle on the small workloads: M_eo and CG on M^dag M to 1e-10
+    at 8^4 (kappa = 0.125, Haar links) and 16^4 (kappa = 0.13, exp(i 0.4 H)
+    links), on all host cores and on one core. A one-core CG is skipped, with
+    its estimate, when the all-core time says it would take over budget_s."""
+    import gen
+    import oracle
+
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "cpu_model": cpu_model()}
+    for dims, kappa, kind in (((8, 8, 8, 8), 0.125, "haar"), ((16, 16, 16, 16), 0.13, "smooth")):
+        U = gen.gauge_field(dims, kind, seed=0, eps=0.4)
+        b = gen.gaussian_spinor(dims, seed=0)[0]
+        V = int(np.prod(dims))
+        ent = {"kappa": kappa, "links": kind}
+        t_cg_all = None
+        for threads in (cores, 1):
+            oracle.set_threads(threads)
+            key = "all_cores" if threads == cores else "one_core"
+            reps, t0 = 0, time.perf_counter()
+            while reps < 3 or time.perf_counter() - t0 < 0.5:
+                oracle.meo(U, kappa, b, dims)
+                reps += 1
+            dt = (time.perf_counter() - t0) / reps
+            row = {"meo_ms": round(dt * 1e3, 3),
+                   "meo_gflops": round(FLOP_PER_SITE * V / dt / 1e9, 3)}
+            est = None if t_cg_all is None else t_cg_all * dt / ent["all_cores"]["meo_ms"] * 1e3
+            if threads == 1 and est is not None and est > budget_s:
+                row["cg_skipped"] = f"estimated {est:.0f} s on one core"
+            else:
+                t0 = time.perf_counter()
+                _, it, rr, ok = oracle.cg(U, kappa, b, dims, tol=1e-10, maxiter=20000)
+                tcg = time.perf_counter() - t0
+                if threads == cores:
+                    t_cg_all = tcg
+                row.update({"cg_seconds": round(tcg, 3), "cg_iterations": it, "cg_true_relres": rr,
+                            "cg_converged": ok})
+            ent[key] = row
+        out["x".join(map(str, dims))] = ent
+    oracle.set_threads(cores)
+    return out
 
 
 # wall-clock budget of a whole reference-arm run (warm-up plus timed steps)

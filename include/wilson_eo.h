@@ -29,7 +29,9 @@
  *                                    (planar: each of the 12 spin-colour
  *                                    components is a contiguous array of V/2
  *                                    sites), complex128 for WEO_F64 handles and
- *                                    complex64 for WEO_F32 / WEO_F16 / WEO_BF16
+ *                                    complex64 for WEO_F32 / WEO_F16 / WEO_BF16;
+ *                                    wilson_eo_spinor_layout converts from and
+ *                                    to the site-major psi[rhs][i][spin][colour]
  *   force   F[mu][lex][a][b]         like the gauge field, in the spinor dtype
  *
  * Pointers: every array argument may be device memory (cudaMalloc / torch) or
@@ -218,6 +220,13 @@ int wilson_eo_solver_config(wilson_eo_t h, double delta, int chunk, int use_grap
  * decides convergence; mode 0 with the native FP64 operator every time. Plain
  * FP64 solves always use the native FP64 operator. Other modes: WEO_ERR_ARG. */
 int wilson_eo_solver_residual(wilson_eo_t h, int mode);
+
+/* Search direction of the mixed-precision solver after a reliable update:
+ * restart 0 (default) keeps it (Clark et al. 2010); restart 1 starts a new
+ * direction from the recomputed residual at every reliable update, which makes
+ * the solve a defect correction whose inner solves reduce the residual by
+ * `delta` each (Sec. 2 leaves the solver open). Other values: WEO_ERR_ARG. */
+int wilson_eo_solver_restart(wilson_eo_t h, int restart);
 
 /* Statistics of the handle's last solve: low-precision (or FP64 in plain mode)
  * CG iterations, reliable updates, native FP64 operator applications (true
@@ -421,6 +430,22 @@ int wilson_eo_profile_read(wilson_eo_t h, int max_kernels, char *names, int name
  * the caller must serialise them. Asynchronous on `stream`. */
 int wilson_eo_apply_noalloc(const int dims[4], double kappa, const void *gauge, void *out_e,
                             const void *in_e, int dag, void *stream);
+
+/* Reorder single-parity spinors between the site-major layout
+ * psi[rhs][i][spin][colour] (each site's 12 spin-colour components together)
+ * and this library's planar layout psi[rhs][spin][colour][i] (every call above
+ * takes planar arrays), with the same parity index i = lex/2 (Sec. 3.3) in both.
+ *   half_volume  V/2, the sites of one parity (>= 1)
+ *   nrhs         right-hand sides (1..65535), stored one after the other
+ *   elem_bytes   8 (complex64) or 16 (complex128)
+ *   to_planar    1: src site-major -> dst planar; 0: src planar -> dst site-major
+ *   dst, src     device arrays of half_volume * 12 * nrhs elements; must not overlap
+ * Host arrays, overlapping arrays and values out of range: WEO_ERR_ARG, before
+ * any launch. No counterpart in the paper (it fixes no in-memory order of the
+ * components); a transpose through shared memory, asynchronous on `stream`,
+ * allocates nothing. */
+int wilson_eo_spinor_layout(long long half_volume, int nrhs, int elem_bytes, int to_planar,
+                            void *dst, const void *src, void *stream);
 
 /* Measured arithmetic peak of the current GPU in flop/s (2 per fused
  * multiply-add) for prec WEO_F64 or WEO_F32, written to *flops_per_s. A

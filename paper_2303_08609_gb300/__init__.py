@@ -85,6 +85,8 @@ def _load():
         "wilson_eo_solve_full": (I, [P, P, P, P, P, D, I, I, IP, ctypes.POINTER(D), P]),
         "wilson_eo_solve_stats": (I, [P, IP, IP, IP, IP, ctypes.POINTER(D)]),
         "wilson_eo_solver_residual": (I, [P, I]),
+        "wilson_eo_solver_restart": (I, [P, I]),
+        "wilson_eo_spinor_layout": (I, [ctypes.c_longlong, I, I, I, P, P, P]),
         "wilson_eo_apply_ff64": (I, [P, P, P, I, I, P]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(P), I, P]),
@@ -430,6 +432,37 @@ def wilson_eo_solver_residual(h, mode):
     """True residuals of reliable updates: 1 float-float (FP64 confirms
     convergence), 0 native FP64."""
     _check(_load().wilson_eo_solver_residual(h, int(mode)), "wilson_eo_solver_residual")
+
+
+def wilson_eo_spinor_layout(dst, src, to_planar=True, stream=None):
+    """Reorder device spinors between site-major (..., V/2, 4, 3) and planar
+    (..., 4, 3, V/2): ``to_planar`` reads site-major ``src`` into planar ``dst``,
+    otherwise the reverse. Both complex64 or both complex128, same size."""
+    shape = tuple(src.shape)
+    if len(shape) < 3:
+        raise ValueError("spinor arrays need at least 3 dimensions")
+    if to_planar and shape[-2:] != (4, 3):
+        raise ValueError(f"site-major src must end in (4, 3), got {shape}")
+    if not to_planar and shape[-3:-1] != (4, 3):
+        raise ValueError(f"planar src must end in (4, 3, V/2), got {shape}")
+    vh = shape[-3] if to_planar else shape[-1]
+    nrhs = int(np.prod(shape[:-3])) if len(shape) > 3 else 1
+    dt = _dtype_name(src)
+    if dt not in ("complex64", "complex128") or _dtype_name(dst) != dt:
+        raise TypeError(f"wilson_eo_spinor_layout: complex64 or complex128 arrays of one dtype, "
+                        f"got {dt} and {_dtype_name(dst)}")
+    if _nbytes(dst) != _nbytes(src):
+        raise ValueError("wilson_eo_spinor_layout: dst and src differ in size")
+    elem = 8 if dt == "complex64" else 16
+    _check(_load().wilson_eo_spinor_layout(int(vh), int(nrhs), elem, int(bool(to_planar)), _ptr(dst),
+                                           _ptr(src), _stream(stream)),
+           "wilson_eo_spinor_layout")
+
+
+def wilson_eo_solver_restart(h, restart):
+    """Mixed solver: 1 restarts the search direction at every reliable update
+    (defect correction), 0 keeps it (default)."""
+    _check(_load().wilson_eo_solver_restart(h, int(restart)), "wilson_eo_solver_restart")
 
 
 def wilson_eo_apply_ff64(h, out_e, in_e, nrhs=1, dag=False, stream=None):

@@ -763,6 +763,17 @@ int wilson_eo_solver_residual(wilson_eo_t h, int mode)
     }
 }
 
+int wilson_eo_solver_restart(wilson_eo_t h, int restart)
+{
+    try {
+        if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+        DeviceGuard dg(h->device);
+        return solver_restart_mode(h, restart);
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_solver_restart");
+    }
+}
+
 void wilson_eo_destroy(wilson_eo_t h)
 {
     if (!h) return;

@@ -75,6 +75,7 @@ struct SolverState {
     int use_graphs = 1;
     int nrhs = 1;                    // right-hand sides of the current solve
     int ff_residual = 1;             // mixed mode: reliable updates with the float-float operator
+    int restart_on_update = 0;       // mixed mode: every reliable update restarts the direction
     // statistics of the last solve
     int iterations = 0, reliable_updates = 0, hi_applies = 0, ff_applies = 0;
     double seconds = 0.0;
@@ -784,7 +785,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
             if (n_active == 0) break;
             k_convert<float2, double2><<<flat_grid(nt), 256, 0, s>>>((float2 *)S->rs.ptr, (const double2 *)S->r64.ptr, nt);
             for (int r = 0; r < R; ++r)
-                if (active[r] && restart[r])
+                if (active[r] && (restart[r] || S->restart_on_update))
                     WEO_CUDA(cudaMemcpyAsync(static_cast<char *>(S->p.ptr) + r * v32,
                                              static_cast<const char *>(S->rs.ptr) + r * v32, v32,
                                              cudaMemcpyDeviceToDevice, s));
@@ -869,6 +870,15 @@ int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi
     if (hi_applies) *hi_applies = S ? S->hi_applies : 0;
     if (ff_applies) *ff_applies = S ? S->ff_applies : 0;
     if (seconds) *seconds = S ? S->seconds : 0.0;
+    return WEO_OK;
+}
+
+int solver_restart_mode(wilson_eo_s *h, int restart)
+{
+    if (restart != 0 && restart != 1) return set_error(WEO_ERR_ARG, "restart must be 0 or 1");
+    SolverState *S = nullptr;
+    WEO_TRY(solver_state(h, &S));
+    S->restart_on_update = restart;
     return WEO_OK;
 }
 

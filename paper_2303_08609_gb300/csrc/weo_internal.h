@@ -191,6 +191,7 @@ int solver_configure(wilson_eo_s *h, double delta, int chunk, int use_graphs);
 int solver_stats(wilson_eo_s *h, int *iterations, int *reliable_updates, int *hi_applies,
                  int *ff_applies, double *seconds);
 int solver_residual_mode(wilson_eo_s *h, int mode);
+int solver_restart_mode(wilson_eo_s *h, int restart);
 void solver_destroy(wilson_eo_s *h);
 int prepare_source_device(wilson_eo_s *h, void *rhs_e, const void *eta_e, const void *eta_o,
                           cudaStream_t s);

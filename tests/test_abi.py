@@ -150,3 +150,18 @@ def test_noalloc_refuses_tensors_off_the_gpu_before_the_library(lib):
     assert weo._noalloc_device((OnGpu(1), OnGpu(1), None)) == 1
     with pytest.raises(ValueError, match="different devices"):
         weo.wilson_eo_apply_noalloc((4, 4, 4, 4), 0.1, OnGpu(0), OnGpu(1), OnGpu(0))
+
+
+def test_spinor_layout_rejects_bad_arguments_before_the_device(lib):
+    n = 8
+    a = np.zeros(12 * n, dtype=np.complex64)
+    b = np.zeros(12 * n, dtype=np.complex64)
+    P = a.ctypes.data
+    Q = b.ctypes.data
+    assert lib.wilson_eo_spinor_layout(n, 1, 8, 1, None, Q, None) == -1
+    assert lib.wilson_eo_spinor_layout(0, 1, 8, 1, P, Q, None) == -1
+    assert lib.wilson_eo_spinor_layout(n, 0, 8, 1, P, Q, None) == -1
+    assert lib.wilson_eo_spinor_layout(n, 1, 4, 1, P, Q, None) == -1
+    assert lib.wilson_eo_spinor_layout(n, 1, 8, 2, P, Q, None) == -1
+    assert lib.wilson_eo_spinor_layout(n, 1, 8, 1, P, P + 8, None) == -1  # overlapping
+    assert lib.wilson_eo_spinor_layout(n, 1, 8, 1, P, Q, None) == -1      # host arrays
