@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--solve-dims", type=int, nargs=4, default=[48, 48, 48, 96])
     ap.add_argument("--solve-variants", nargs="*", default=None,
                     help="only these entries of the solve comparison (e.g. mixed_f16_two_pass)")
+    ap.add_argument("--only-multi-rhs", type=int, default=0, metavar="N",
+                    help="run only M_eo then M_eo^dag on N Gaussian right-hand sides (launch "
+                         "configuration autotuned for N) and print its timing; for profiling")
     ap.add_argument("--dims", type=int, nargs=4, default=None,
                     help="lattice extents (default 32 32 32 64, the benchmark workload)")
     args = ap.parse_args()
@@ -307,14 +310,13 @@ def run_ours(args, rank, world, local):
 
             dist.barrier()
 
-    free0 = torch.cuda.mem_get_info(dev)[0]
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     if staged_main(args):
-        # the staged hop's per-tile link blocks (2 x 576 B per even site), built
-        # on first use: device memory they took beside the packed links
-        staged_mb = round((free0 - torch.cuda.mem_get_info(dev)[0]) / 1e6, 1)
+        # the staged hop's per-tile link blocks: 576 B per site of each output
+        # parity, beside the packed links (counted in device_mb too)
+        staged_mb = round(576 * V / 1e6, 1)
     device_mb = round(weo.wilson_eo_info(op.handle).get("device_bytes", 0) / 1e6, 1)
 
     # ---- timed region: device events on the launching stream
@@ -776,7 +778,8 @@ def multi_solve_comparison(U, dev):
 
 # solves of the default run (the others are selectable with --solve-variants)
 DEFAULT_SOLVES = ("mixed_f16_fused", "mixed_bf16_fused", "mixed_f32_fused", "mixed_f16_two_pass",
-                  "mixed_f16_l12_two_pass", "mixed_f16_l12_tuned", "plain_f64")
+                  "mixed_f16_l12_two_pass", "mixed_f16_l12_tuned", "mixed_bf16_l12_two_pass",
+                  "mixed_bf16_two_pass_keep", "plain_f64")
 
 
 def oracle_relres(U, kappa, x, b, dims):
@@ -820,8 +823,8 @@ def solve_comparison(dev, dims, only=None):
                                     ("mixed_f16_l12_tuned", "f16", True, 0),
                                     ("mixed_bf16_two_pass", "bf16", True, 0),
                                     ("mixed_bf16_l12_two_pass", "bf16", True, 0),
-                                    ("mixed_bf16_restart", "bf16", True, 0),
-                                    ("mixed_bf16_l12_restart", "bf16", True, 0),
+                                    ("mixed_bf16_two_pass_keep", "bf16", True, 0),
+                                    ("mixed_bf16_l12_two_pass_keep", "bf16", True, 0),
                                     ("mixed_f16_l12_restart", "f16", True, 0),
                                     ("plain_f64", "f64", False, 0),
                                     ("plain_f64_tuned", "f64", False, 0)):
@@ -836,6 +839,8 @@ def solve_comparison(dev, dims, only=None):
             weo.wilson_eo_solver_residual(op.handle, 0)
         if "restart" in name:  # defect correction: new direction at every reliable update
             weo.wilson_eo_solver_restart(op.handle, 1)
+        if name.endswith("_keep"):  # directions kept across reliable updates
+            weo.wilson_eo_solver_restart(op.handle, 0)
         if name.endswith("_tuned"):  # autotuned operator (tuning not timed)
             weo.wilson_eo_tune(op.handle, nrhs=1)
             res.setdefault("tuned", {})[name] = {**weo.wilson_eo_get_algorithm(op.handle),
@@ -1008,9 +1013,50 @@ def run_reference(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def multi_rhs_only(args, local):
+    """M_eo then M_eo^dag on args.only_multi_rhs Gaussian right-hand sides
+    (seed 0), operator autotuned for that count; CUDA-event timing of
+    args.steps steps after args.warmup."""
+    import torch
+
+    import gen
+    import paper_2303_08609_gb300 as weo
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.only_multi_rhs
+    U = gen.gauge_field(DIMS, "smooth", seed=0, eps=EPS)
+    V = int(np.prod(DIMS))
+    op = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec, linkfmt=args.linkfmt)
+    del U
+    x = torch.from_numpy(np.ascontiguousarray(np.moveaxis(gen.gaussian_spinor(DIMS, nrhs=n, seed=0), 1, -1))
+                         .astype(np.complex128 if args.prec == "f64" else np.complex64)).to(dev)
+    y, z = torch.empty_like(x), torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    weo.wilson_eo_tune(op.handle, n, stream)
+    t, rb, lanes = weo.wilson_eo_get_launch(op.handle)
+
+    def step():
+        weo.wilson_eo_apply(op.handle, y, x, n, stream)
+        weo.wilson_eo_apply_dag(op.handle, z, y, n, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ms = timed(step, args.steps, stream)
+    op.close()
+    print(json.dumps({"nrhs": n, "lattice": list(DIMS), "prec": args.prec, "linkfmt": args.linkfmt,
+                      "threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
+                      "ms_per_step": round(ms, 4),
+                      "gflops": round(n * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.only_multi_rhs:
+        multi_rhs_only(args, local)
+        return
     if args.only_solve:
         import torch
 

@@ -460,8 +460,8 @@ def wilson_eo_spinor_layout(dst, src, to_planar=True, stream=None):
 
 
 def wilson_eo_solver_restart(h, restart):
-    """Mixed solver: 1 restarts the search direction at every reliable update
-    (defect correction), 0 keeps it (default)."""
+    """Mixed solver, search direction at a reliable update: 1 restart (defect
+    correction), 0 keep, 2 (default) restart for BF16 inner operators only."""
     _check(_load().wilson_eo_solver_restart(h, int(restart)), "wilson_eo_solver_restart")
 
 
