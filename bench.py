@@ -661,9 +661,18 @@ def extras(U, psi, dev, stream):
                             weo.wilson_eo_apply_dag(op.handle, z, y, 12, stream)), 50, stream)
         res[f"rhs_per_thread_{rb}"] = {"ms_per_step": round(ms, 4),
                                        "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
+    weo.wilson_eo_set_launch(op.handle, 128, 1)
+    for nrl in (2, 4, 8):  # tiles with their links in shared memory, nrl RHS per pass
+        weo.wilson_eo_set_tile_links(op.handle, nrl)
+        ms = timed(lambda: (weo.wilson_eo_apply(op.handle, y, x, 12, stream),
+                            weo.wilson_eo_apply_dag(op.handle, z, y, 12, stream)), 50, stream)
+        res[f"tile_links_{nrl}"] = {"ms_per_step": round(ms, 4),
+                                    "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
+    weo.wilson_eo_set_tile_links(op.handle, 0)
     t, rb, tms = weo.wilson_eo_tune(op.handle, 12, stream)
     lanes = weo.wilson_eo_get_launch(op.handle)[2]
-    res["tuned"] = {"threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes, "ms_per_meo": round(tms, 4),
+    res["tuned"] = {"threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
+                    "tile_links": weo.wilson_eo_get_tile_links(op.handle), "ms_per_meo": round(tms, 4),
                     "gflops": round(12 * FLOP_PER_SITE * V / (tms * 1e-3) / 1e9, 1),
                     "two_pass_model_bytes": int((576 + 240 * 12) * V),
                     "two_pass_model_frac": round((576 + 240 * 12) * V / (tms * 1e-3) / 1e9
@@ -680,6 +689,7 @@ def extras(U, psi, dev, stream):
                         weo.wilson_eo_apply_dag(op.handle, z, y, 16, stream)), 20, stream)
     out["multi_rhs_16_f32"] = {"rhs": "12 spin-colour point sources + 4 Gaussian (seed 9)",
                                "threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
+                               "tile_links": weo.wilson_eo_get_tile_links(op.handle),
                                "ms_per_step": round(ms, 4),
                                "gflops": round(16 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1),
                                "two_pass_model_frac": round(2 * (576 + 240 * 16) * V / (ms * 1e-3) / 1e9
@@ -753,7 +763,7 @@ def multi_solve_comparison(U, dev):
         weo.wilson_eo_tune(op.handle, nrhs=12)
         threads, rb, lanes = weo.wilson_eo_get_launch(op.handle)
         cfg = dict(weo.wilson_eo_get_algorithm(op.handle), threads=threads, rhs_per_thread=rb,
-                   rhs_lanes=lanes)
+                   rhs_lanes=lanes, tile_links=weo.wilson_eo_get_tile_links(op.handle))
         try:
             x, info = op.solve(b, tol=1e-10, maxiter=20000, mixed=mixed)
             res[name] = {"seconds": round(info["seconds"], 4), "iterations": info["iterations"],
@@ -1035,6 +1045,7 @@ def multi_rhs_only(args, local):
     stream = torch.cuda.current_stream(dev)
     weo.wilson_eo_tune(op.handle, n, stream)
     t, rb, lanes = weo.wilson_eo_get_launch(op.handle)
+    tl = weo.wilson_eo_get_tile_links(op.handle)
 
     def step():
         weo.wilson_eo_apply(op.handle, y, x, n, stream)
@@ -1046,7 +1057,7 @@ def multi_rhs_only(args, local):
     ms = timed(step, args.steps, stream)
     op.close()
     print(json.dumps({"nrhs": n, "lattice": list(DIMS), "prec": args.prec, "linkfmt": args.linkfmt,
-                      "threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
+                      "threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes, "tile_links": tl,
                       "ms_per_step": round(ms, 4),
                       "gflops": round(n * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}), flush=True)
 

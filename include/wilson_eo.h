@@ -386,6 +386,21 @@ int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order);
  * on an FP64 handle. */
 int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes);
 
+/* Several right-hand sides with each tile's links loaded once (the batching
+ * pattern of the multi-RHS hop; Table 1's tiling sweep is the paper's
+ * analogue, Sec. 4): a CTA of 256 threads takes a tile of 256 / rhs_per_pass
+ * consecutive output sites, copies the eight links of every tile site into
+ * shared memory (as FP32, 576 bytes per site), and then passes over the tile
+ * rhs_per_pass right-hand sides at a time until all nrhs are done; spinors are
+ * read from global memory. rhs_per_pass 2, 4 or 8 turns it on for the
+ * handle's FP32 or 16-bit hops whenever nrhs >= 2 (and sets one right-hand
+ * side per thread); 0 (default) turns it off. WEO_ERR_ARG for other values,
+ * WEO_ERR_UNSUPPORTED on an FP64 handle. wilson_eo_tune times these
+ * configurations too. */
+int wilson_eo_set_tile_links(wilson_eo_t h, int rhs_per_pass);
+/* The handle's current rhs_per_pass (0 = off). */
+int wilson_eo_get_tile_links(wilson_eo_t h, int *rhs_per_pass);
+
 /* M_eo in_e (dag = 0) or M_eo^dag in_e (dag = 1) in float-float arithmetic:
  * every real is carried as an unevaluated sum hi + lo of two floats (about 48
  * significant bits; error-free two-sum and FMA-based two-product), so the

@@ -86,6 +86,8 @@ def _load():
         "wilson_eo_solve_stats": (I, [P, IP, IP, IP, IP, ctypes.POINTER(D)]),
         "wilson_eo_solver_residual": (I, [P, I]),
         "wilson_eo_solver_restart": (I, [P, I]),
+        "wilson_eo_set_tile_links": (I, [P, I]),
+        "wilson_eo_get_tile_links": (I, [P, P]),
         "wilson_eo_spinor_layout": (I, [ctypes.c_longlong, I, I, I, P, P, P]),
         "wilson_eo_apply_ff64": (I, [P, P, P, I, I, P]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -432,6 +434,18 @@ def wilson_eo_solver_residual(h, mode):
     """True residuals of reliable updates: 1 float-float (FP64 confirms
     convergence), 0 native FP64."""
     _check(_load().wilson_eo_solver_residual(h, int(mode)), "wilson_eo_solver_residual")
+
+
+def wilson_eo_set_tile_links(h, rhs_per_pass):
+    """Multi-RHS hops over tiles whose links sit in shared memory, rhs_per_pass
+    (2, 4, 8) right-hand sides at a time; 0 turns it off."""
+    _check(_load().wilson_eo_set_tile_links(h, int(rhs_per_pass)), "wilson_eo_set_tile_links")
+
+
+def wilson_eo_get_tile_links(h):
+    n = ctypes.c_int(0)
+    _check(_load().wilson_eo_get_tile_links(h, ctypes.byref(n)), "wilson_eo_get_tile_links")
+    return n.value
 
 
 def wilson_eo_spinor_layout(dst, src, to_planar=True, stream=None):

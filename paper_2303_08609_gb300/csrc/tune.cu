@@ -1,13 +1,15 @@
 // Autotuner for M_eo: times each candidate on the handle's own lattice and
 // keeps the fastest. Candidates: the two-launch algorithm with 64..256 threads
 // per CTA and (FP32 / 16-bit handles with several right-hand sides) 1, 2 or 4
-// right-hand sides per thread, or two right-hand sides on neighbouring lanes;
+// right-hand sides per thread, or two right-hand sides on neighbouring lanes,
+// or tiles whose links sit in shared memory for 2, 4 or 8 right-hand sides at
+// a time;
 // and, for FP32 / 16-bit handles, the fused single-launch algorithm with a
 // lookahead of 4 or 8 t-slices and 128 or 256 threads per CTA. Results are
 // cached per process, keyed by (GPU name, extents, precision, link format,
 // nrhs), and optionally in a text file named by the environment variable
-// WILSON_EO_TUNE_CACHE (one "v3 key algo threads rhs_block lanes lookahead ms"
-// line each).
+// WILSON_EO_TUNE_CACHE (one "v5 key algo threads rhs_block lanes lookahead ms
+// staged tile_links" line each; v3 and v4 lines are still read).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -26,6 +28,7 @@ struct TuneEntry {
     int algo, threads, rhs_block, lanes, lookahead;
     double ms;
     int staged = 0;  // FP32 18-real hops through the TMA-staged kernel
+    int tile_links = 0;  // several RHS over tiles with links in shared memory
 };
 
 static std::mutex g_tune_mutex;
@@ -61,7 +64,9 @@ static void load_tune_file()
     char line[640], key[400];
     while (fgets(line, sizeof(line), f)) {
         TuneEntry e;
-        if (sscanf(line, "v4 %399s %d %d %d %d %d %lf %d", key, &e.algo, &e.threads, &e.rhs_block,
+        if (sscanf(line, "v5 %399s %d %d %d %d %d %lf %d %d", key, &e.algo, &e.threads, &e.rhs_block,
+                   &e.lanes, &e.lookahead, &e.ms, &e.staged, &e.tile_links) == 9 ||
+            sscanf(line, "v4 %399s %d %d %d %d %d %lf %d", key, &e.algo, &e.threads, &e.rhs_block,
                    &e.lanes, &e.lookahead, &e.ms, &e.staged) == 8 ||
             sscanf(line, "v3 %399s %d %d %d %d %d %lf", key, &e.algo, &e.threads, &e.rhs_block,
                    &e.lanes, &e.lookahead, &e.ms) == 7)
@@ -76,8 +81,8 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "v4 %s %d %d %d %d %d %.6f %d\n", key.c_str(), e.algo, e.threads, e.rhs_block,
-            e.lanes, e.lookahead, e.ms, e.staged);
+    fprintf(f, "v5 %s %d %d %d %d %d %.6f %d %d\n", key.c_str(), e.algo, e.threads, e.rhs_block,
+            e.lanes, e.lookahead, e.ms, e.staged, e.tile_links);
     fclose(f);
 }
 
@@ -91,6 +96,7 @@ static int apply_entry(wilson_eo_s *h, const TuneEntry &e, cudaStream_t s)
         h->cfg[h->prec].threads = e.threads;
         h->cfg[h->prec].rhs_block = e.rhs_block;
         h->cfg[h->prec].lanes = e.lanes;
+        h->cfg[h->prec].tile_links = e.tile_links;
     }
     if (h->prec == WEO_F32) {
         h->cfg[WEO_F32].staged = e.staged;
@@ -141,7 +147,8 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     const int saved_algo = h->algo, saved_la = h->fused_lookahead, saved_fthreads = h->fused_threads;
     Profiler *saved_prof = h->prof;
     h->prof = nullptr;
-    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30, saved.staged};
+    TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30, saved.staged,
+                      saved.tile_links};
     std::vector<TuneEntry> cands;
     for (int threads : {64, 128, 192, 256}) {
         for (int r : rb) cands.push_back({0, threads, r, 1, 0, 0.0});
@@ -152,6 +159,9 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
             for (int threads : {128, 256}) cands.push_back({1, threads, 1, 1, la, 0.0});
     if (h->prec == WEO_F32 && h->fmt == WEO_LINK18 && nrhs == 1 && staged_eligible(h))
         cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
+    if (h->prec != WEO_F64 && nrhs >= 2)
+        for (int n : {2, 4, 8})
+            if (n <= 2 * nrhs) cands.push_back({0, 256, 1, 1, 0, 0.0, 0, n});
     for (const TuneEntry &c : cands) {
         if (apply_entry(h, c, s) != WEO_OK) {
             (void)cudaGetLastError();

@@ -262,4 +262,131 @@ __global__ void __launch_bounds__(256, 4) hop_kernel_lanes(const HopParams p)
     hop_site<SIn, SOut, SX, Lk, Dag, Axpy, 1>(p, i, r);
 }
 
+// ------------------------------------------------ links shared per tile --
+// Several right-hand sides with each tile's links loaded once: a CTA of 256
+// threads owns a tile of T = 256 / NRL consecutive output sites. It first
+// copies the eight links of every tile site -- U_mu(x) and U_mu(x - mu) for the
+// backward hop -- into shared memory (converted to FP32 complex, [8][9][T],
+// 576 T bytes), then its NRL groups of T threads take the right-hand sides
+// rhs0 = 0 .. NRL-1 and step by NRL, one (site, right-hand side) per thread,
+// with the spinors read from global memory as in hop_kernel. A link leaves
+// global memory once per tile instead of once per right-hand-side block.
+
+// compact indices of the 8 neighbours of site i (order: +x, -x, +y, -y, +z,
+// -z, +t, -t), as in hop_site
+__device__ __forceinline__ void site_neighbours(const HopParams &p, int i, int nb[8])
+{
+    int rem = i;
+    const int xh = rem % p.lxh;
+    rem /= p.lxh;
+    const int y = rem % p.ly;
+    rem /= p.ly;
+    const int z = rem % p.lz;
+    const int t = rem / p.lz;
+    const int par = (y + z + t + p.out_parity) & 1;
+    const int sy = p.lxh, sz = p.lxh * p.ly, st = p.lxh * p.ly * p.lz;
+    const int row = i - xh;
+    nb[0] = row + (par ? (xh + 1 == p.lxh ? 0 : xh + 1) : xh);
+    nb[1] = row + (par ? xh : (xh == 0 ? p.lxh - 1 : xh - 1));
+    nb[2] = i + (y + 1 == p.ly ? -(p.ly - 1) * sy : sy);
+    nb[3] = i + (y == 0 ? (p.ly - 1) * sy : -sy);
+    nb[4] = i + (z + 1 == p.lz ? -(p.lz - 1) * sz : sz);
+    nb[5] = i + (z == 0 ? (p.lz - 1) * sz : -sz);
+    nb[6] = i + (t + 1 == p.lt ? -(p.lt - 1) * st : st);
+    nb[7] = i + (t == 0 ? (p.lt - 1) * st : -st);
+}
+
+// one hopping direction with the link from shared memory (9 complex at
+// stride T from lk)
+template <class SIn, int MU, bool FWD, int S0>
+__device__ __forceinline__ void hop_dir_shared(cx<float> (&acc)[12], const HopParams &p, int nb,
+                                               const float2 *lk, int T, int rhs)
+{
+    constexpr int S = FWD ? S0 : -S0;
+    cx<float> U[3][3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 u = lk[k * T];
+        U[k / 3][k % 3] = {u.x, u.y};
+    }
+    cx<float> v[12];
+    SIn::load(static_cast<const char *>(p.in) + rhs * p.in_stride, p.vh, nb, v);
+    cx<float> h[2][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
+    cx<float> w[2][3];
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<float> z = {0.f, 0.f};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[sp][b], z) : cfmaconj(U[b][a], h[sp][b], z);
+            w[sp][a] = z;
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        reconstruct<MU, S>(acc[c], acc[3 + c], acc[6 + c], acc[9 + c], w[0][c], w[1][c]);
+}
+
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL>
+__global__ void __launch_bounds__(256, 3) hop_kernel_tile_links(const HopParams p)
+{
+    constexpr int T = 256 / NRL;
+    extern __shared__ __align__(16) float2 lk_sm[];  // [8 directions][9 complex][T]
+    const int ntiles = (int)gridDim.x;
+    const int tile = p.reverse ? ntiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
+    const int i0 = tile * T;
+    const int in_par = p.out_parity ^ 1;
+    // the tile's links: direction d = 2 mu + b, U_mu(x) (b = 0) or U_mu(x - mu) (b = 1)
+    for (int e = threadIdx.x; e < 8 * T; e += 256) {
+        const int d = e / T, s = e - d * T;
+        const int i = i0 + s;
+        if (i >= p.vh) continue;
+        const int mu = d >> 1;
+        int idx = i;
+        if (d & 1) {
+            int nb[8];
+            site_neighbours(p, i, nb);
+            idx = nb[d];
+        }
+        cx<float> U[3][3];
+        Lk::load(p.gauge + (2 * mu + ((d & 1) ? in_par : p.out_parity)) * p.gauge_pb, p.vh, idx, U);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) lk_sm[(d * 9 + k) * T + s] = make_float2(U[k / 3][k % 3].r, U[k / 3][k % 3].i);
+    }
+    __syncthreads();
+    const int s = (int)threadIdx.x % T, rl = (int)threadIdx.x / T;
+    const int i = i0 + s;
+    if (i >= p.vh) return;
+    constexpr int S0 = Dag ? -1 : 1;
+    const float2 *lk = lk_sm + s;
+    for (int r = rl; r < p.nrhs; r += NRL) {
+        int nb[8];
+        site_neighbours(p, i, nb);
+        cx<float> acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+        hop_dir_shared<SIn, 0, true, S0>(acc, p, nb[0], lk + 0 * 9 * T, T, r);
+        hop_dir_shared<SIn, 0, false, S0>(acc, p, nb[1], lk + 1 * 9 * T, T, r);
+        hop_dir_shared<SIn, 1, true, S0>(acc, p, nb[2], lk + 2 * 9 * T, T, r);
+        hop_dir_shared<SIn, 1, false, S0>(acc, p, nb[3], lk + 3 * 9 * T, T, r);
+        hop_dir_shared<SIn, 2, true, S0>(acc, p, nb[4], lk + 4 * 9 * T, T, r);
+        hop_dir_shared<SIn, 2, false, S0>(acc, p, nb[5], lk + 5 * 9 * T, T, r);
+        hop_dir_shared<SIn, 3, true, S0>(acc, p, nb[6], lk + 6 * 9 * T, T, r);
+        hop_dir_shared<SIn, 3, false, S0>(acc, p, nb[7], lk + 7 * 9 * T, T, r);
+        if (Axpy) {
+            cx<float> xv[12];
+            SX::load(static_cast<const char *>(p.x) + r * p.x_stride, p.vh, i, xv);
+            const float a = float(p.a);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                acc[k].r = fmaf(a, acc[k].r, xv[k].r);
+                acc[k].i = fmaf(a, acc[k].i, xv[k].i);
+            }
+        }
+        SOut::store(static_cast<char *>(p.out) + r * p.out_stride, p.vh, i, acc);
+    }
+}
+
 }  // namespace weo

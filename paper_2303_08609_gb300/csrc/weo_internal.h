@@ -74,6 +74,8 @@ struct LaunchCfg {
     int rhs_block = 1;   // right-hand sides per thread (register blocking)
     int lanes = 1;       // right-hand sides on neighbouring lanes sharing link loads
     int staged = 0;      // FP32 18-real, one RHS: operands staged in shared memory by TMA
+    int tile_links = 0;  // several RHS: right-hand sides per pass over a tile whose links
+                         // sit in shared memory (2, 4 or 8; 0 = off)
 };
 
 struct Profiler;

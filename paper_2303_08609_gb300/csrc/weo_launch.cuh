@@ -19,10 +19,34 @@ int launch_lanes(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
     return WEO_OK;
 }
 
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL>
+int launch_tile_links(const HopParams &p, cudaStream_t s)
+{
+    constexpr int T = 256 / NRL;
+    const size_t smem = (size_t)576 * T;
+    auto kern = hop_kernel_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, NRL>;
+    if (smem > 48 * 1024) {
+        static bool attr_set = false;  // per instance; idempotent if two threads race
+        if (!attr_set) {
+            WEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_set = true;
+        }
+    }
+    kern<<<(unsigned)((p.vh + T - 1) / T), 256, smem, s>>>(p);
+    WEO_CUDA(cudaGetLastError());
+    return WEO_OK;
+}
+
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
 {
     if constexpr (R == 1 && sizeof(typename SOut::real) == 4) {
+        // several right-hand sides over tiles whose links sit in shared memory
+        if (cfg.tile_links && p.nrhs >= 2) {
+            if (cfg.tile_links == 8) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 8>(p, s);
+            if (cfg.tile_links == 4) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 4>(p, s);
+            return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 2>(p, s);
+        }
         // right-hand sides sharing link loads across lanes (never more lanes than
         // right-hand sides)
         int nl = cfg.lanes;

@@ -165,3 +165,8 @@ def test_spinor_layout_rejects_bad_arguments_before_the_device(lib):
     assert lib.wilson_eo_spinor_layout(n, 1, 8, 2, P, Q, None) == -1
     assert lib.wilson_eo_spinor_layout(n, 1, 8, 1, P, P + 8, None) == -1  # overlapping
     assert lib.wilson_eo_spinor_layout(n, 1, 8, 1, P, Q, None) == -1      # host arrays
+
+
+def test_tile_links_rejects_null(lib):
+    assert lib.wilson_eo_set_tile_links(None, 4) == -1
+    assert lib.wilson_eo_get_tile_links(None, None) == -1
