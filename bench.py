@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--only-multi-rhs", type=int, default=0, metavar="N",
                     help="run only M_eo then M_eo^dag on N Gaussian right-hand sides (launch "
                          "configuration autotuned for N) and print its timing; for profiling")
+    ap.add_argument("--tile-links", type=int, default=-1, metavar="N",
+                    help="with --only-multi-rhs: hops over tiles with links in shared memory, N "
+                         "right-hand sides per pass (0: off); default: autotuned")
     ap.add_argument("--dims", type=int, nargs=4, default=None,
                     help="lattice extents (default 32 32 32 64, the benchmark workload)")
     args = ap.parse_args()
@@ -1025,8 +1028,8 @@ def run_reference(args, rank, world, local):
 
 def multi_rhs_only(args, local):
     """M_eo then M_eo^dag on args.only_multi_rhs Gaussian right-hand sides
-    (seed 0), operator autotuned for that count; CUDA-event timing of
-    args.steps steps after args.warmup."""
+    (seed 0), operator autotuned for that count (or with args.tile_links fixed);
+    CUDA-event timing of args.steps steps after args.warmup."""
     import torch
 
     import gen
@@ -1043,7 +1046,10 @@ def multi_rhs_only(args, local):
                          .astype(np.complex128 if args.prec == "f64" else np.complex64)).to(dev)
     y, z = torch.empty_like(x), torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
-    weo.wilson_eo_tune(op.handle, n, stream)
+    if args.tile_links >= 0:
+        weo.wilson_eo_set_tile_links(op.handle, args.tile_links)
+    else:
+        weo.wilson_eo_tune(op.handle, n, stream)
     t, rb, lanes = weo.wilson_eo_get_launch(op.handle)
     tl = weo.wilson_eo_get_tile_links(op.handle)
 
