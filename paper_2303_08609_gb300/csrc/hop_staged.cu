@@ -35,6 +35,7 @@
 #include <mutex>
 
 #include "weo_internal.h"
+#include "weo_tma.cuh"
 
 namespace weo {
 
@@ -110,100 +111,11 @@ bool make_layout(int lxh, int rows, bool axpy, StageLayout &L)
     return staged_smem(L, 2) <= kSmemLimit;
 }
 
-// ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ unsigned smem_addr(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
-{
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // wait for the phase of `bar` with the given parity to complete, at most
 // limit_ns nanoseconds; false (and the error word set) on expiry
 __device__ __noinline__ bool mbar_wait(uint64_t *bar, unsigned parity, const StagedParams &P)
 {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > P.limit_ns) {
-            atomicOr(P.err, 1u);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                       uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_hint(void *dst, const void *src, unsigned bytes, uint64_t *bar,
-                                          uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                       uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
-        : "memory");
+    return mbar_wait_bounded(bar, parity, P.limit_ns, P.err);
 }
 
 // ---------------------------------------------------------------- tiles --
@@ -257,51 +169,6 @@ __device__ __forceinline__ void issue_tile(const StagedParams &P, int j, char *b
     tma_2d(base + L.sp[5], &P.sp_tile, 2 * row_start(P, g.z, tp, g.y0), 0, full);
     tma_2d(base + L.sp[6], &P.sp_tile, 2 * row_start(P, g.z, tm, g.y0), 0, full);
     if (Axpy) tma_2d(base + L.x, &P.x_tile, 2 * i0, 0, full);
-}
-
-// one hopping direction from shared memory: spinor planes of stride `ss`
-// (complex) at index si, link planes of stride `ls` at index li
-template <int MU, bool FWD, int S0>
-__device__ __forceinline__ void staged_dir(cx<float> (&acc)[12], const float2 *sp, int ss, int si,
-                                           const float4 *l4, const float2 *l2, int ls, int li)
-{
-    constexpr int S = FWD ? S0 : -S0;
-    const float4 a = l4[li], b = l4[ls + li], c = l4[2 * ls + li], d = l4[3 * ls + li];
-    const float2 e = l2[li];
-    cx<float> U[3][3];
-    U[0][0] = {a.x, a.y};
-    U[0][1] = {a.z, a.w};
-    U[0][2] = {b.x, b.y};
-    U[1][0] = {b.z, b.w};
-    U[1][1] = {c.x, c.y};
-    U[1][2] = {c.z, c.w};
-    U[2][0] = {d.x, d.y};
-    U[2][1] = {d.z, d.w};
-    U[2][2] = {e.x, e.y};
-    cx<float> v[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float2 q = sp[k * ss + si];
-        v[k] = {q.x, q.y};
-    }
-    cx<float> h[2][3];
-#pragma unroll
-    for (int col = 0; col < 3; ++col)
-        project<MU, S>(v[col], v[3 + col], v[6 + col], v[9 + col], h[0][col], h[1][col]);
-    cx<float> w[2][3];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            cx<float> zz = {0.f, 0.f};
-#pragma unroll
-            for (int col = 0; col < 3; ++col)
-                zz = FWD ? cfma(U[r][col], h[s][col], zz) : cfmaconj(U[col][r], h[s][col], zz);
-            w[s][r] = zz;
-        }
-#pragma unroll
-    for (int col = 0; col < 3; ++col)
-        reconstruct<MU, S>(acc[col], acc[3 + col], acc[6 + col], acc[9 + col], w[0][col], w[1][col]);
 }
 
 template <bool Dag, bool Axpy, int NS>
@@ -651,39 +518,6 @@ __global__ void pack_link_blocks_kernel(const HopParams p, int T, float *out)
         }
 }
 
-// -------------------------------------------------------- tensor maps --
-using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encoder()
-{
-    static std::once_flag once;
-    static EncodeFn fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeFn>(p);
-    });
-    return fn;
-}
-
-// FP32 tensor of rank 2 or 3 (dims[0] contiguous; strides in bytes of dims 1..)
-bool encode(CUtensorMap *m, const void *ptr, int rank, const cuuint64_t *dims,
-            const cuuint64_t *strides, const cuuint32_t *box)
-{
-    EncodeFn fn = encoder();
-    if (!fn) return false;
-    const cuuint32_t one[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(ptr), dims,
-              strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 // rows of R per tile: R divides Ly, R >= 2, R * Lx/2 <= 64; the largest such
 // R, or the requested one when it qualifies (0 if none does)
 int staged_rows(int lxh, int ly, int want = 0)
@@ -782,6 +616,34 @@ int launch_depth(bool dag, bool axpy, const StagedParams &P, int grid, cudaStrea
 
 }  // namespace
 
+// -------------------------------------------------------- tensor maps --
+EncodeFn tma_encoder()
+{
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+// FP32 tensor of rank 2 or 3 (dims[0] contiguous; strides in bytes of dims 1..)
+bool tma_encode(CUtensorMap *m, const void *ptr, int rank, const cuuint64_t *dims,
+            const cuuint64_t *strides, const cuuint32_t *box)
+{
+    EncodeFn fn = tma_encoder();
+    if (!fn) return false;
+    const cuuint32_t one[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(ptr), dims,
+              strides, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // tile rows and ring depth a handle's staged hops use (0, 0 if not eligible)
 void staged_shape(const wilson_eo_s *h, int *rows_out, int *depth_out)
 {
@@ -800,7 +662,7 @@ bool staged_eligible(const wilson_eo_s *h)
 {
     int rows, depth;
     staged_shape(h, &rows, &depth);
-    return depth > 0 && encoder() != nullptr;
+    return depth > 0 && tma_encoder() != nullptr;
 }
 
 bool staged_arrays_ok(const HopParams &p, bool axpy)
@@ -887,8 +749,8 @@ int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, c
     const int rank = nrhs > 1 ? 3 : 2;
     if (nrhs > 1 && ((p.in_stride & 15) || (axpy && (p.x_stride & 15)) || (p.out_stride & 7)))
         return set_error(WEO_ERR_UNSUPPORTED, "staged hop: right-hand-side strides not aligned");
-    bool ok = encode(&P.sp_tile, p.in, rank, sd, ss, b_tile) && encode(&P.sp_row, p.in, rank, sd, ss, b_row);
-    if (ok && axpy) ok = encode(&P.x_tile, p.x, rank, sd, sx, b_tile);
+    bool ok = tma_encode(&P.sp_tile, p.in, rank, sd, ss, b_tile) && tma_encode(&P.sp_row, p.in, rank, sd, ss, b_row);
+    if (ok && axpy) ok = tma_encode(&P.x_tile, p.x, rank, sd, sx, b_tile);
     if (!ok) return set_error(WEO_ERR_CUDA, "staged hop: tensor map encoding failed");
     P.links = blocks + (long long)p.out_parity * 576 * vh;
     P.lxh = lxh;

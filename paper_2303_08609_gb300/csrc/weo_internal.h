@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libwilson_eo.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -160,6 +161,17 @@ int staged_prepare(wilson_eo_s *h, const PackedGauge &g, cudaStream_t s);
 bool staged_ready(wilson_eo_s *h, const HopParams &p, cudaStream_t s);
 int launch_hop_staged(wilson_eo_s *h, bool dag, bool axpy, const HopParams &p, cudaStream_t s,
                       bool inject = false);
+
+// tensor maps (hop_staged.cu): cuTensorMapEncodeTiled through the runtime's
+// driver entry point (null if unavailable); FP32 tensor of rank 2 or 3,
+// dims[0] contiguous, strides in bytes of dims 1..
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn tma_encoder();
+bool tma_encode(CUtensorMap *m, const void *ptr, int rank, const cuuint64_t *dims,
+                const cuuint64_t *strides, const cuuint32_t *box);
 
 // launch_hop for a handle, with its launch configuration and profiling
 int handle_hop(wilson_eo_s *h, int prec, int fmt, int io, bool dag, bool axpy, const HopParams &p,
