@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--linkfmt", type=int, default=18)
-    ap.add_argument("--algo", type=int, default=0, help="0: two hop launches, 1: fused")
+    ap.add_argument("--algo", type=int, default=0,
+                    help="0: two hop launches, 1: fused, 2: fused through the TMA-staged pipeline")
     ap.add_argument("--lookahead", type=int, default=4,
                     help="t-slices the fused kernel's first hop runs ahead of the second")
     ap.add_argument("--staged", action=argparse.BooleanOptionalAction, default=True,
@@ -132,6 +133,8 @@ HOP_SOURCES = ("weo_fields.cuh", "weo_dslash.cuh", "weo_launch.cuh", "dslash_f32
 
 def sources_for(label):
     """Source files a kernel label's code comes from."""
+    if label.startswith("fused_staged"):
+        return HOP_SOURCES + ("fused_staged.cu", "weo_tma.cuh")
     if label.startswith("fused_"):
         return HOP_SOURCES + ("fused.cu",)
     if label.startswith("hop_staged"):
@@ -230,6 +233,10 @@ def stored_traffic(label):
 # (V/2 output sites): input spinors once + all 4V links once + output once,
 # + the axpy addend for the second hop.
 def algo_bytes_per_site(label):
+    if label.startswith("fused_staged_"):
+        # one M_eo: even input once, every link once (the pair blocks are read
+        # by both hops, the second time from L2), even output once
+        return 96 / 2 + 4 * 72 + 96 / 2
     if label.startswith("fused_"):
         # one M_eo: even input once, all 4V links once, even output once (FP32 spinors)
         lk = {"f32": 72, "f16": 36, "bf16": 36}[label.split("_")[1]]
@@ -290,7 +297,8 @@ def run_ours(args, rank, world, local):
 
     def configure(o):
         if args.algo:
-            weo.wilson_eo_set_algorithm(o.handle, "fused", args.lookahead, 128)
+            weo.wilson_eo_set_algorithm(o.handle, {1: "fused", 2: "fused_staged"}[args.algo],
+                                        args.lookahead, 128)
         weo.wilson_eo_set_launch(o.handle, args.threads, 1, args.order)
         if staged_main(args):
             weo.wilson_eo_set_staging(o.handle, True, args.staged_rows, args.staged_depth)
@@ -453,9 +461,10 @@ def run_ours(args, rank, world, local):
     variants = {}
     if not args.no_variants:
         Ud = torch.from_numpy(U).to(dev)
-        # algo 0: two hop launches, 1: fused, 2: two staged (TMA) hop launches
-        main = (args.prec, args.linkfmt, 2 if staged_main(args) else args.algo)
-        for prec, fmt, algo in (("f32", 18, 0), ("f32", 18, 2), ("f32", 12, 0), ("f16", 18, 0),
+        # algo 0: two hop launches, 1: fused, 2: two staged (TMA) hop launches,
+        # 3: fused staged (one TMA-fed launch)
+        main = (args.prec, args.linkfmt, 2 if staged_main(args) else {2: 3}.get(args.algo, args.algo))
+        for prec, fmt, algo in (("f32", 18, 0), ("f32", 18, 2), ("f32", 18, 3), ("f32", 12, 0), ("f16", 18, 0),
                                 ("f16", 12, 0), ("bf16", 12, 0), ("f64", 18, 0), ("f32", 18, 1),
                                 ("f32", 12, 1), ("f16", 18, 1), ("f16", 12, 1), ("bf16", 12, 1)):
             if (prec, fmt, algo) == main:
@@ -465,6 +474,8 @@ def run_ours(args, rank, world, local):
                 weo.wilson_eo_set_algorithm(o2.handle, "fused", args.lookahead, 128)
             if algo == 2:
                 weo.wilson_eo_set_staging(o2.handle, True)
+            if algo == 3:
+                weo.wilson_eo_set_algorithm(o2.handle, "fused_staged", 2)
             xv = torch.from_numpy(np.ascontiguousarray(np.moveaxis(psi, 0, -1))).to(dev) \
                 if prec == "f64" else x
             yv, zv = torch.empty_like(xv), torch.empty_like(xv)
@@ -502,7 +513,7 @@ def run_ours(args, rank, world, local):
             if yo is not None:
                 ent["meo_rel_l2_64_sites"] = float(np.linalg.norm(yo - want_y)
                                                    / np.linalg.norm(want_y))
-            variants[f"{prec}_l{fmt}" + ("", "_fused", "_staged")[algo]] = ent
+            variants[f"{prec}_l{fmt}" + ("", "_fused", "_staged", "_fused_staged")[algo]] = ent
             o2.close()
             del xv, yv, zv
         # the same step on fully Haar-random links (seed 0): FP32 18-real staged
@@ -585,7 +596,7 @@ def run_ours(args, rank, world, local):
                       "bf16": "bf16-storage/f32"}[args.prec],
             "data": "synthetic",
             "config": workload_config(args, world),
-            "impl_config": {"algo": "fused" if args.algo else
+            "impl_config": {"algo": {1: "fused", 2: "fused staged (TMA)"}.get(args.algo) if args.algo else
                                     "two staged (TMA) hop launches" if staged_main(args)
                                     else "two hop launches",
                             "threads": args.threads,

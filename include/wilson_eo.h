@@ -284,10 +284,22 @@ int wilson_eo_tune(wilson_eo_t h, int nrhs, int *threads_out, int *rhs_block_out
  *           in L2; `threads` per CTA 128 or 256 (0 keeps the current value).
  *           Same arithmetic and intermediate format as algo 0, so the
  *           results are bitwise equal.
+ *   algo 2  the same wavefront of both hops in one persistent launch fed by
+ *           the tensor-memory accelerator (FP32 handles with 18-real links and
+ *           lattices the staged hop tiles, see wilson_eo_set_staging): per tile
+ *           item one producer thread copies the neighbour spinor rows (tensor
+ *           boxes) and the tile's links into a ring of shared-memory stages,
+ *           and second-hop items wait until the first-hop items of slices
+ *           t-1, t, t+1 have published. The links of both hops come from one
+ *           pair block per tile (each link stored once, plus the row below
+ *           each tile: 576 T + 144 Lx/2 bytes per tile of T sites), so a link
+ *           leaves HBM once per M_eo. The blocks are built on first use (not
+ *           while the stream is being captured) and after set_gauge.
+ *           `lookahead` as for algo 1; `threads` is ignored.
  * Items wait for the items they depend on with bounded polling; if a wait ever
  * gives up (about a second without progress), the kernel records an error
  * that wilson_eo_check reports as WEO_ERR_TIMEOUT. FP64 handles: algo 1 gives
- * WEO_ERR_UNSUPPORTED. */
+ * WEO_ERR_UNSUPPORTED; algo 2 gives it for any handle it cannot serve. */
 int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads);
 
 /* Failure-path test of the fused kernel: runs one fused M_eo in which the
@@ -295,7 +307,11 @@ int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads)
  * the poll limit is short (~0.3 ms), so the second-hop items' bounded waits run
  * out; the kernel records the error and every CTA returns. wilson_eo_check then
  * reports WEO_ERR_TIMEOUT. out_e receives garbage. Nothing faults, traps or
- * hangs; the context stays usable. FP32 / 16-bit handles, device arrays. */
+ * hangs; the context stays usable. FP32 / 16-bit handles, device arrays. With
+ * algo 2 selected (wilson_eo_set_algorithm) the same test runs the fused
+ * staged launch: its first-hop tiles never publish, the producers' bounded
+ * waits for them give up after ~2 ms, every consumer group is stopped and the
+ * CTAs return. */
 int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e, void *stream);
 
 /* Hopping kernel fed by TMA (Eq. 1 for one parity, as wilson_eo_hop; used by

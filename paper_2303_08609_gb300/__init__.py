@@ -528,8 +528,9 @@ def wilson_eo_tune(h, nrhs=1, stream=None):
 
 def wilson_eo_set_algorithm(h, algo, lookahead=0, threads=0):
     """algo 0: two hop launches; 1: fused single launch, the first hop running
-    ``lookahead`` t-slices ahead of the second."""
-    a = {"two_pass": 0, "fused": 1}.get(algo, algo)
+    ``lookahead`` t-slices ahead of the second; 2 ("fused_staged"): the same
+    wavefront through the TMA-staged pipeline (FP32 18-real handles)."""
+    a = {"two_pass": 0, "fused": 1, "fused_staged": 2}.get(algo, algo)
     _check(_load().wilson_eo_set_algorithm(h, int(a), int(lookahead), int(threads)),
            "wilson_eo_set_algorithm")
 

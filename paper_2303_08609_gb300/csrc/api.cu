@@ -170,6 +170,14 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
              int nrhs, bool dag, cudaStream_t s)
 {
     const int prec = g.prec;
+    if (h->algo == 2 && prec == WEO_F32 && g.fmt == WEO_LINK18) {
+        const long long ext32 = h->vh * 96;
+        WEO_TRY(tmp.ensure((size_t)ext32));
+        for (int r = 0; r < nrhs; ++r)
+            WEO_TRY(meo_fstaged(h, g, tmp.ptr, static_cast<char *>(out) + r * ext32,
+                                static_cast<const char *>(in) + r * ext32, dag, s));
+        return WEO_OK;
+    }
     if (h->algo == 1 && prec != WEO_F64 && prec != kPrecFF) {
         const long long ext32 = h->vh * 96;
         WEO_TRY(tmp.ensure((size_t)h->vh * (prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16))));
@@ -478,9 +486,14 @@ int wilson_eo_inject_staged_timeout(wilson_eo_t h, void *out_o, const void *in_e
 int wilson_eo_set_algorithm(wilson_eo_t h, int algo, int lookahead, int threads)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
-    if (algo != 0 && algo != 1) return set_error(WEO_ERR_ARG, "algo must be 0 (two launches) or 1 (fused)");
+    if (algo < 0 || algo > 2)
+        return set_error(WEO_ERR_ARG, "algo must be 0 (two launches), 1 (fused) or 2 (fused staged)");
     if (algo == 1 && h->prec == WEO_F64)
         return set_error(WEO_ERR_UNSUPPORTED, "the fused M_eo has FP32 arithmetic only");
+    if (algo == 2 && !fstaged_eligible(h))
+        return set_error(WEO_ERR_UNSUPPORTED,
+                         "the fused staged M_eo needs an FP32 handle with 18-real links and a lattice "
+                         "the staged tiles cover (Lx/2 even, rows of at most 64 sites dividing Ly)");
     if (lookahead != 0 && (lookahead < 1 || lookahead > 64))
         return set_error(WEO_ERR_ARG, "lookahead must be 0 or in 1..64");
     if (threads != 0 && threads != 128 && threads != 256)
@@ -500,6 +513,9 @@ int wilson_eo_inject_fused_timeout(wilson_eo_t h, void *out_e, const void *in_e,
             return set_error(WEO_ERR_ARG, "device arrays only");
         DeviceGuard dg(h->device);
         WEO_TRY(h->tmp.ensure((size_t)h->vh * (h->prec == WEO_F32 ? 96 : spinor_site_bytes(SK_H16))));
+        if (h->algo == 2)
+            return meo_fstaged(h, h->gauge, h->tmp.ptr, out_e, in_e, false, static_cast<cudaStream_t>(stream),
+                               true);
         return meo_fused(h, h->gauge, h->tmp.ptr, out_e, in_e, false, static_cast<cudaStream_t>(stream), true);
     } catch (...) {
         return set_error(WEO_ERR_OOM, "host exception in wilson_eo_inject_fused_timeout");
@@ -534,7 +550,7 @@ int wilson_eo_info(wilson_eo_t h, int dims_out[4], long long *half_volume, int *
         *device_bytes = h->gauge.buf.bytes + h->gauge_f64.buf.bytes + h->gauge_lo.buf.bytes +
                         h->gauge_ff.buf.bytes + h->ff_in.bytes + h->ff_out.bytes + h->ff_tmp.bytes +
                         h->canon_gauge.bytes + h->tmp.bytes + h->tmp2.bytes + h->tmp3.bytes +
-                        h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes + h->staged_links.bytes +
+                        h->even1.bytes + h->fused_ctrl.bytes + h->halo.bytes + h->staged_links.bytes + h->fs_links.bytes +
                         h->stage_in.bytes +
                         h->stage_out.bytes + h->stage_aux.bytes;
     return WEO_OK;
@@ -810,6 +826,7 @@ void wilson_eo_destroy(wilson_eo_t h)
     h->tmp2.release();
     h->tmp3.release();
     h->staged_links.release();
+    h->fs_links.release();
     h->even1.release();
     h->stage_in.release();
     h->stage_out.release();

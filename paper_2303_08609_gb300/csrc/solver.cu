@@ -721,6 +721,7 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
     } else {
         WEO_TRY(lo_gauge(h, &glo, s));
         WEO_TRY(staged_prepare(h, *glo, s));  // before any capture
+        WEO_TRY(fstaged_prepare(h, *glo, s));
         const bool restart_all = S->restart_on_update == 1 ||
                                  (S->restart_on_update == 2 && glo->prec == WEO_BF16);
         WEO_TRY(S->xs.ensure(b32));
@@ -845,7 +846,7 @@ int solve_device(wilson_eo_s *h, void *x_e, const void *b_e, bool x_host, bool b
     // every buffer an iteration touches exists before a graph is captured
     WEO_TRY(S->oddlo.ensure((size_t)h->vh * 96 * nrhs));
     WEO_TRY(S->odd64.ensure(b64));
-    if (h->algo == 1) WEO_TRY(fused_prepare(h, S->stream));
+    if (h->algo == 1 || h->algo == 2) WEO_TRY(fused_prepare(h, S->stream));
     // order after the caller's prior work, then run on the solver's own stream
     WEO_CUDA(cudaStreamSynchronize(user));
     cudaStream_t s = S->stream;

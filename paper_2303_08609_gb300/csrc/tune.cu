@@ -5,7 +5,8 @@
 // or tiles whose links sit in shared memory for 2, 4 or 8 right-hand sides at
 // a time;
 // and, for FP32 / 16-bit handles, the fused single-launch algorithm with a
-// lookahead of 4 or 8 t-slices and 128 or 256 threads per CTA. Results are
+// lookahead of 4 or 8 t-slices and 128 or 256 threads per CTA; for FP32 18-real
+// handles the fused staged launch with a lookahead of 2 or 4. Results are
 // cached per process, keyed by (GPU name, extents, precision, link format,
 // nrhs), and optionally in a text file named by the environment variable
 // WILSON_EO_TUNE_CACHE (one "v5 key algo threads rhs_block lanes lookahead ms
@@ -89,7 +90,7 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
 static int apply_entry(wilson_eo_s *h, const TuneEntry &e, cudaStream_t s)
 {
     h->algo = e.algo;
-    if (e.algo == 1) {
+    if (e.algo == 1 || e.algo == 2) {
         h->fused_threads = e.threads;
         h->fused_lookahead = e.lookahead;
     } else {
@@ -159,6 +160,8 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
             for (int threads : {128, 256}) cands.push_back({1, threads, 1, 1, la, 0.0});
     if (h->prec == WEO_F32 && h->fmt == WEO_LINK18 && nrhs == 1 && staged_eligible(h))
         cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
+    if (fstaged_eligible(h))
+        for (int la : {2, 4}) cands.push_back({2, 128, 1, 1, la, 0.0});
     if (h->prec != WEO_F64 && nrhs >= 2)
         for (int n : {2, 4, 8})
             if (n <= 2 * nrhs) cands.push_back({0, 256, 1, 1, 0, 0.0, 0, n});
@@ -181,7 +184,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
             (void)cudaGetLastError();
             continue;
         }
-        if (c.algo == 1 || c.staged) {
+        if (c.algo == 1 || c.algo == 2 || c.staged) {
             unsigned int err = 0;
             if (fused_take_error(h, s, &err) != WEO_OK || err) continue;
         }
@@ -207,6 +210,10 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     if (!h->cfg[WEO_F32].staged) {  // the trial's link blocks are not kept
         h->staged_links.release();
         h->staged_valid = false;
+    }
+    if (h->algo != 2) {
+        h->fs_links.release();
+        h->fs_valid = false;
     }
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -105,7 +105,8 @@ struct wilson_eo_s {
     weo::LaunchCfg cfg[5];       // per operator precision (weo_prec, then kPrecFF)
     weo::Profiler *prof = nullptr;
     weo::SolverState *solver = nullptr;
-    // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused
+    // M_eo algorithm for FP32 / 16-bit operators: 0 two hop launches, 1 fused,
+    // 2 fused through the TMA-staged pipeline (FP32 18-real)
     int algo = 0;
     int alternate = 1;       // second hop walks the sites in reverse order
     int fused_lookahead = 4;     // t-slices the fused kernel's first hop runs ahead
@@ -117,6 +118,11 @@ struct wilson_eo_s {
     unsigned staged_gen = 0;           // ... at this pack generation,
     int staged_tile = 0;               // ... for tiles of this many sites
     bool staged_valid = false;
+    weo::Buffer fs_links;    // fused staged M_eo: pair link blocks of both parities
+    const void *fs_src = nullptr;  // ... packed from this field,
+    unsigned fs_gen = 0;           // ... at this pack generation,
+    int fs_tile = 0;               // ... for tiles of this many sites
+    bool fs_valid = false;
     weo::Buffer fused_ctrl;  // sticky error, ticket, completion counters
     weo::Buffer halo;        // face buffers of the domain-decomposed hop
 };
@@ -186,6 +192,12 @@ int meo_with(wilson_eo_s *h, const PackedGauge &g, Buffer &tmp, void *out, const
 int meo_fused(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, const void *in, bool dag,
               cudaStream_t s, bool inject_timeout = false);
 int fused_take_error(wilson_eo_s *h, cudaStream_t s, unsigned int *err);
+// fused_staged.cu: both hops in one persistent launch fed by TMA, pair link
+// blocks shared by the two hops (FP32 18-real, one right-hand side)
+bool fstaged_eligible(const wilson_eo_s *h);
+int fstaged_prepare(wilson_eo_s *h, const PackedGauge &g, cudaStream_t s);
+int meo_fstaged(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, const void *in, bool dag,
+                cudaStream_t s, bool inject = false);
 int fused_prepare(wilson_eo_s *h, cudaStream_t s);
 // halo.cu: hop with the lattice split along t and every crossing hop exchanged
 int hop_split_device(wilson_eo_s *h, int ranks, int out_parity, bool dag, void *out,

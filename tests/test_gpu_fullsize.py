@@ -31,12 +31,14 @@ KAPPA = 0.13
 #   staged: two TMA-staged hop launches (the benchmark's main line)
 #   plain : two one-site-per-thread hop launches
 #   fused : one persistent launch over a wavefront of t-slices
+#   fused_staged: the same wavefront through the TMA-staged pipeline
 #   ff    : float-float arithmetic on an FP64 handle
 PATHS = [
     ("f32_l18_staged", "f32", 18, "staged"),
     ("f32_l18_two_launch", "f32", 18, "plain"),
     ("f32_l12_two_launch", "f32", 12, "plain"),
     ("f32_l18_fused", "f32", 18, "fused"),
+    ("f32_l18_fused_staged", "f32", 18, "fused_staged"),
     ("f32_l12_fused", "f32", 12, "fused"),
     ("f16_l18_two_launch", "f16", 18, "plain"),
     ("f16_l12_two_launch", "f16", 12, "plain"),
@@ -98,6 +100,8 @@ def test_meo_whole_lattice(weo, fields_32x64, reference, name, prec, fmt, path):
         assert weo.wilson_eo_get_staging(op.handle)["staged"]
     elif path == "fused":
         weo.wilson_eo_set_algorithm(op.handle, "fused", 4, 128)
+    elif path == "fused_staged":
+        weo.wilson_eo_set_algorithm(op.handle, "fused_staged", 2)
     spin = "f64" if prec == "f64" else "f32"
     x = to_device(to_planar(psi), spin)
     for dag in (False, True):

@@ -435,3 +435,141 @@ def test_staged_protocol_check_catches_groups_sharing_stages():
         except AssertionError:
             caught += 1
     assert caught > 0
+
+
+# ---------------------------------------------------------------------------
+# Fused staged M_eo: pair link blocks shared by both hops. Each tile j (R rows
+# of one (z, t) plane, T sites of each parity) has one block with the fields
+#   eYh | oZ oT oX oY eX eY eZ eT | oYh
+# (o/e: links at the tile's odd/even sites, Yh: U_y at the row below the tile).
+# A first-hop item (odd output) copies eYh..eY of its block plus eZ of the tile
+# in plane z-1 and eT of the tile in plane t-1; a second-hop item (even output)
+# copies oX..oYh plus oZ and oT of those tiles. The model below follows the
+# kernel's field offsets, copy ranges and consumer indices, and checks every
+# link and spinor a consumer reads against the neighbour rule.
+
+def pair_fields(T, lxh):
+    f = {"eYh": 0, "oZ": 72 * lxh}
+    for a, b in (("oT", "oZ"), ("oX", "oT"), ("oY", "oX"), ("eX", "oY"), ("eY", "eX"), ("eZ", "eY"),
+                 ("eT", "eZ"), ("oYh", "eT")):
+        f[a] = f[b] + 72 * T
+    f["bytes"] = f["oYh"] + 72 * lxh
+    return f
+
+
+def pack_pair_blocks(dims, rows):
+    """byte offset in the block array -> (packed field 2 mu + parity, compact
+    index) of the link stored there (first float of each link)."""
+    lx, ly, lz, lt = dims
+    lxh, vh = lx // 2, lx * ly * lz * lt // 2
+    T = rows * lxh
+    f = pair_fields(T, lxh)
+    mem = {}
+    for gi in range(vh):
+        j, s = divmod(gi, T)
+        base = j * f["bytes"]
+        for name, fi in (("oX", 1), ("oY", 3), ("oZ", 5), ("oT", 7), ("eX", 0), ("eY", 2), ("eZ", 4), ("eT", 6)):
+            mem[base + f[name] + 16 * s] = (fi, gi)
+        if s < lxh:
+            plane, y0 = divmod(j * rows, ly)
+            h = (plane * ly + (y0 - 1) % ly) * lxh + s
+            mem[base + f["eYh"] + 16 * s] = (2, h)
+            mem[base + f["oYh"] + 16 * s] = (3, h)
+    return mem, f
+
+
+def fs_item(dims, rows, lookahead, q):
+    lx, ly, lz, lt = dims
+    tpp = ly // rows
+    tps = lz * tpp
+    k, c = divmod(q, tps)
+    kind, t = fused_task(lt, lookahead, k)
+    z, yb = divmod(c, tpp)
+    y0 = yb * rows
+    j = t * tps + c
+    jzm = t * tps + ((z - 1) % lz) * tpp + y0 // rows
+    jtm = ((t - 1) % lt) * tps + c
+    return kind == "B", t, z, y0, j, jzm, jtm
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 4, 6, 6), (8, 8, 8, 8), (16, 2, 4, 4), (12, 6, 4, 8),
+                                  (4, 6, 2, 22), (32, 8, 2, 4), (24, 8, 2, 2), (32, 4, 4, 2)])
+def test_fused_staged_reads(dims):
+    lx, ly, lz, lt = dims
+    lxh = lx // 2
+    rows = staged_rows(lxh, ly)
+    if not rows:
+        pytest.skip("not tileable")
+    T = rows * lxh
+    mem, f = pack_pair_blocks(dims, rows)
+    tps = lz * (ly // rows)
+    seen = set()
+    for q in range(2 * lt * tps):
+        b, t, z, y0, j, jzm, jtm = fs_item(dims, rows, 1, q)
+        seen.add((b, j))
+        # the stage's link region: three copies (destination offset = block offset)
+        stage = {}
+
+        def copy(src_tile, off, size):
+            for o in range(off, off + size, 16):
+                key = src_tile * f["bytes"] + o
+                if key in mem:
+                    stage[o] = mem[key]
+
+        if not b:
+            copy(j, 0, f["eY"] + 72 * T)
+            copy(jzm, f["eZ"], 72 * T)
+            copy(jtm, f["eT"], 72 * T)
+        else:
+            copy(j, f["oX"], f["bytes"] - f["oX"])
+            copy(jzm, f["oZ"], 72 * T)
+            copy(jtm, f["oT"], 72 * T)
+        out_parity = 0 if b else 1
+        o, e = ("e", "o") if b else ("o", "e")
+        fwd = {mu: f[o + "XYZT"[mu]] for mu in range(4)}
+        bwd = {mu: f[e + "XYZT"[mu]] for mu in range(4)}
+        bwd_halo = f[e + "Yh"]
+        boxes, geo = staged_boxes(dims, rows, j)
+        assert geo[:3] == (y0, z, t)
+        for s in range(T):
+            i = j * T + s
+            nb, _ = kernel_neighbours(dims, out_parity, i)
+            r, xh = divmod(s, lxh)
+            for (mu, sgn), region, idx, _d in staged_reads(dims, rows, geo, s, out_parity):
+                first, n = boxes[region]
+                assert 0 <= idx < n and first + idx == nb[(mu, sgn)]  # spinor read
+                if sgn > 0:
+                    off, lidx, n_l = fwd[mu], s, T
+                elif mu == 0:
+                    off, lidx, n_l = bwd[0], r * lxh + (idx - r * lxh), T
+                elif mu == 1 and r == 0:
+                    off, lidx, n_l = bwd_halo, xh, lxh
+                elif mu == 1:
+                    off, lidx, n_l = bwd[1], s - lxh, T
+                else:
+                    off, lidx, n_l = bwd[mu], s, T
+                assert 0 <= lidx < n_l
+                want = (2 * mu + out_parity, i) if sgn > 0 else (2 * mu + (out_parity ^ 1), nb[(mu, -1)])
+                assert stage[off + 16 * lidx] == want, (dims, b, j, s, mu, sgn)
+    assert len(seen) == 2 * lt * tps  # every tile once per hop
+
+
+@pytest.mark.parametrize("lt", [2, 3, 4, 7, 16])
+@pytest.mark.parametrize("lookahead", [1, 2, 4])
+def test_fused_staged_dependencies_come_first(lt, lookahead):
+    """Every second-hop tile's dependencies (all first-hop tiles of slices t-1,
+    t, t+1) hold earlier tickets, so the earliest unfinished item never waits."""
+    dims = (4, 4, 2, lt)
+    rows = staged_rows(2, 4)
+    la = max(1, min(lookahead, lt - 1))
+    tps = dims[2] * (dims[1] // rows)
+    first = {}
+    for q in range(2 * lt * tps):
+        b, t, *_ = fs_item(dims, rows, la, q)
+        if not b:
+            first.setdefault(t, []).append(q)
+    for q in range(2 * lt * tps):
+        b, t, *_ = fs_item(dims, rows, la, q)
+        if b:
+            for dt in (-1, 0, 1):
+                assert max(first[(t + dt) % lt]) < q
