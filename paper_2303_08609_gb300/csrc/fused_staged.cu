@@ -5,13 +5,16 @@
 // plane, T = R Lx/2 sites of each parity). Work items are
 //   A(tile): tmp = H_oe in onto the tile's odd sites, and
 //   B(tile): out = in - kappa^2 H_eo tmp onto the tile's even sites,
-// taken from one atomic ticket in the wavefront order of the fused kernel:
-// slice tasks A(Lt-1), A(0) .. A(D-1), then A(t+D) and B(t) in turn, each task
-// the tiles of one t-slice. B(t) reads the intermediate at slices t-1, t and
-// t+1, so the producer issues its loads only after A(t-1), A(t), A(t+1) have
-// published completion; a ticket is handed out only after all earlier ones
-// and every wait is for an earlier ticket, so the earliest unfinished item
-// never waits (every wait is bounded all the same).
+// in the wavefront order of the fused kernel: slice tasks A(Lt-1), A(0) ..
+// A(D-1), then A(t+D) and B(t) in turn, each task the tiles of one t-slice.
+// The queue is dealt round robin to the CTAs (one per SM, all resident: the
+// launch is cooperative), each taking its items in queue order. B(t) reads the
+// intermediate at slices t-1, t and t+1, so the producer issues its loads only
+// after A(t-1), A(t), A(t+1) have published completion (slices it has seen
+// complete are remembered). Every wait is for items earlier in the queue, and
+// every CTA works through its items in queue order, so the earliest unfinished
+// item never waits and the launch always progresses (every wait is bounded all
+// the same).
 //
 // Links: one pair block per tile holds the links owned by the tile's sites of
 // both parities, each link stored once: fields (4 float4 planes + 1 float2
@@ -120,7 +123,7 @@ struct FsParams {
     const float2 *in;    // even input (axpy addend of B)
     float2 *mid;         // odd intermediate
     float2 *out;         // even output
-    unsigned int *ctrl;  // [0] sticky error, [1] ticket, [2] this launch's error, [3 ..) per-slice counts
+    unsigned int *ctrl;  // [0] sticky error, [1] unused, [2] this launch's error, [3 ..) per-slice counts
     unsigned long long limit_ns;
     int inject;          // failure-path test: A items never publish completion
 };
@@ -289,27 +292,32 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mid_row)) : "memory");
         const uint64_t pol = policy_evict_first();
         const unsigned need = (unsigned)(P.tps * P.tpt);  // team stores of one slice
+        int known[4] = {-1, -1, -1, -1};  // slices seen complete (most recent four)
+        int kn = 0;
         int k = 0;
-        bool ok = true;
         for (;; ++k) {
             const int s = k % NS, u = k / NS;
-            if (u >= 1 && !fs_mbar_wait(empty + s, (unsigned)((u - 1) & 1), P)) {
-                ok = false;
-                break;
-            }
-            const int q = ok ? (int)atomicAdd(P.ctrl + 1, 1u) : P.total;
-            if (q >= P.total) break;
+            if (u >= 1 && !fs_mbar_wait(empty + s, (unsigned)((u - 1) & 1), P)) break;
+            // items in queue order, round robin over the co-resident CTAs
+            const long long qq = (long long)blockIdx.x + (long long)k * gridDim.x;
+            if (qq >= P.total) break;
+            const int q = (int)qq;
             const FsItem it = fs_item(P, q);
             if (it.b) {
                 const int tm = it.t == 0 ? P.lt - 1 : it.t - 1, tp = it.t + 1 == P.lt ? 0 : it.t + 1;
-                if (!fs_wait_count(P, 3 + tm, need) || !fs_wait_count(P, 3 + it.t, need) ||
-                    !fs_wait_count(P, 3 + tp, need)) {
-                    ok = false;
-                    break;
+                const int need_t[3] = {tm, it.t, tp};
+                bool ok = true, waited = false;
+                for (int d = 0; d < 3 && ok; ++d) {
+                    const int tt = need_t[d];
+                    if (tt == known[0] || tt == known[1] || tt == known[2] || tt == known[3]) continue;
+                    ok = fs_wait_count(P, 3 + tt, need);
+                    waited = true;
+                    if (ok) known[kn++ & 3] = tt;
                 }
+                if (!ok) break;
                 // the intermediate was written by generic stores: order them before
                 // the tensor copies that read it
-                asm volatile("fence.proxy.async.global;" ::: "memory");
+                if (waited) asm volatile("fence.proxy.async.global;" ::: "memory");
             }
             slot[s] = q;
             fs_issue(P, it, smem + s * L.bytes, full + s, pol);
@@ -475,9 +483,13 @@ __global__ void pack_pair_blocks_kernel(const HopParams p, int rows, char *out)
     }
 }
 
+// One CTA per SM, launched cooperatively: the static round-robin schedule
+// relies on every CTA being resident (an item may wait for items of any other
+// CTA), which a cooperative launch guarantees or refuses.
 template <bool Dag, int NS>
-int launch_fs(const FsParams &P, int grid, cudaStream_t s)
+int launch_fs(const FsParams &P, int sms, cudaStream_t s)
 {
+    auto kern = fused_staged_kernel<Dag, NS>;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -486,8 +498,21 @@ int launch_fs(const FsParams &P, int grid, cudaStream_t s)
     });
     WEO_CUDA(attr);
     const int threads = 32 * (2 * NS * P.tpt + 1);
-    fused_staged_kernel<Dag, NS><<<grid, threads, fs_smem(P.L, NS), s>>>(P);
-    WEO_CUDA(cudaGetLastError());
+    const size_t smem = fs_smem(P.L, NS);
+    int per_sm = 0;
+    WEO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return set_error(WEO_ERR_CUDA, "fused staged M_eo: kernel cannot be resident");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)sms);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr_list[1];
+    attr_list[0].id = cudaLaunchAttributeCooperative;
+    attr_list[0].val.cooperative = 1;
+    cfg.attrs = attr_list;
+    cfg.numAttrs = 1;
+    WEO_CUDA(cudaLaunchKernelEx(&cfg, kern, P));
     return WEO_OK;
 }
 
@@ -608,13 +633,12 @@ int meo_fstaged(wilson_eo_s *h, const PackedGauge &g, void *mid, void *out, cons
     P.inject = inject ? 1 : 0;
     int sms = 0;
     WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    const int grid = sms;
     int tok = prof_begin(h, kernel_label("fused_staged", WEO_F32, WEO_LINK18, dag, true).c_str(), s);
     int st;
     if (ns == 3)
-        st = dag ? launch_fs<true, 3>(P, grid, s) : launch_fs<false, 3>(P, grid, s);
+        st = dag ? launch_fs<true, 3>(P, sms, s) : launch_fs<false, 3>(P, sms, s);
     else
-        st = dag ? launch_fs<true, 2>(P, grid, s) : launch_fs<false, 2>(P, grid, s);
+        st = dag ? launch_fs<true, 2>(P, sms, s) : launch_fs<false, 2>(P, sms, s);
     prof_end(h, tok, s);
     return st;
 }

@@ -573,3 +573,37 @@ def test_fused_staged_dependencies_come_first(lt, lookahead):
         if b:
             for dt in (-1, 0, 1):
                 assert max(first[(t + dt) % lt]) < q
+
+
+@pytest.mark.parametrize("grid", [1, 2, 3, 7, 152])
+@pytest.mark.parametrize("lt,lookahead", [(2, 1), (3, 1), (4, 2), (9, 4), (16, 2)])
+def test_fused_staged_round_robin_always_progresses(grid, lt, lookahead):
+    """The fused staged launch deals the queue round robin: CTA c takes items
+    c, c + G, c + 2G, ... in that order and a second-hop item waits until the
+    first-hop tiles of slices t-1, t, t+1 are done. Step all CTAs until every
+    item is done; some CTA must move at every step (no deadlock), whatever the
+    order in which the CTAs run."""
+    dims = (4, 4, 2, lt)
+    rows = staged_rows(2, 4)
+    tps = dims[2] * (dims[1] // rows)
+    total = 2 * lt * tps
+    items = [fs_item(dims, rows, lookahead, q) for q in range(total)]
+    done_a = {t: 0 for t in range(lt)}
+    nxt = list(range(grid))  # next item of each CTA
+    rng = np.random.default_rng(lt * 100 + grid)
+    remaining = total
+    while remaining:
+        moved = False
+        for c in rng.permutation(grid):
+            q = nxt[c]
+            if q >= total:
+                continue
+            b, t, *_ = items[q]
+            if b and any(done_a[(t + d) % lt] < tps for d in (-1, 0, 1)):
+                continue  # waits (bounded in the kernel); other CTAs move
+            if not b:
+                done_a[t] += 1
+            nxt[c] += grid
+            remaining -= 1
+            moved = True
+        assert moved, "no CTA can progress"
