@@ -396,6 +396,11 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
                     acc[c].r += v.x;
                     acc[c].i += v.y;
                 }
+            }
+            // the stage is consumed: hand it back before the global stores
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + g);
+            if (active) {
                 if (it.b) {
                     float2 *o = P.out + it.i0 + s;
 #pragma unroll
@@ -409,16 +414,13 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
             }
             if (!it.b) {
                 // make the intermediate visible to the tensor copies of B items
-                // (async proxy, other CTAs), then count this team's store
+                // (async proxy, other CTAs), then count this team's store with a
+                // release-ordered reduction
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncwarp();
-                if (lane == 0 && !P.inject) {
-                    __threadfence();
-                    atomicAdd(P.ctrl + 3 + it.t, 1u);
-                }
+                if (lane == 0 && !P.inject)
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(P.ctrl + 3 + it.t) : "memory");
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty + g);
         } else {
             if (active) {
                 Field F = field(lk, fZ, T);
