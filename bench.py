@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip multi-RHS, batch and force measurements")
     ap.add_argument("--no-solve", action="store_true", help="skip the 48^3x96 solve comparison")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end measurement (for profiling runs)")
     ap.add_argument("--only-solve", action="store_true", help="run only the solve comparison")
     ap.add_argument("--solve-dims", type=int, nargs=4, default=[48, 48, 48, 96])
     ap.add_argument("--solve-variants", nargs="*", default=None,
@@ -399,7 +401,7 @@ def run_ours(args, rank, world, local):
     # host arrays make the calls asynchronous); the best of them is reported,
     # with the one-stream figure beside it.
     nb = x_host.nbytes
-    NS_E2E = 4  # handles / streams taking the steps in turn
+    NS_E2E = 1 if args.no_e2e else 4  # handles / streams taking the steps in turn
     ops2 = [op]
     for _ in range(NS_E2E - 1):
         o_ = weo.WilsonEO(DIMS, KAPPA, torch.from_numpy(U).to(dev), prec=args.prec,
@@ -423,7 +425,7 @@ def run_ours(args, rank, world, local):
 
     ke = max(6, min(400, args.steps // 4))
     e2e_ms = {}
-    for nstreams in range(1, NS_E2E + 1):
+    for nstreams in range(1, NS_E2E + 1) if not args.no_e2e else ():
         e2e_steps(6, nstreams)
         torch.cuda.synchronize()
         barrier()
@@ -433,8 +435,8 @@ def run_ours(args, rank, world, local):
         e2e_ms[nstreams], e2e_val = replica_summary((time.perf_counter() - t0) * 1e3 / ke, flops_step,
                                                     world, dev)
     zres = np.moveaxis(zh[(ke - 1) % NS_E2E].numpy(), -1, 0)  # the last step's result, read on the host
-    ns = min(range(2, NS_E2E + 1), key=lambda k: e2e_ms[k])
-    e2e = {"value": round(world * flops_step / (e2e_ms[ns] * 1e-3) / 1e9, 1), "unit": "GFlop/s",
+    ns = min(range(2, NS_E2E + 1), key=lambda k: e2e_ms[k]) if not args.no_e2e else 1
+    e2e = None if args.no_e2e else {"value": round(world * flops_step / (e2e_ms[ns] * 1e-3) / 1e9, 1), "unit": "GFlop/s",
            "ms_per_step": round(e2e_ms[ns], 4), "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
            "mode": f"pipelined: {ns} handles on {ns} streams take the steps in turn, each "
                    f"holding its own packed links (and staged link blocks)",

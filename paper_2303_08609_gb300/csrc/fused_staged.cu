@@ -215,8 +215,10 @@ __device__ __forceinline__ int fs_row(const FsParams &P, int z, int t, int y)
 }
 
 // issue the copies of item `it` into the stage at `base`
+// pol_a: link copies of first-hop items (read again by the second hop of the
+// same slices: kept in L2); pol_b: those of second-hop items (last use)
 __device__ __forceinline__ void fs_issue(const FsParams &P, const FsItem &it, char *base, uint64_t *full,
-                                         uint64_t pol)
+                                         uint64_t pol_a, uint64_t pol_b)
 {
     const FsLayout &L = P.L;
     const int T = P.tile;
@@ -232,13 +234,13 @@ __device__ __forceinline__ void fs_issue(const FsParams &P, const FsItem &it, ch
     char *lk = base + L.lk;
     mbar_expect_tx(full, (unsigned)(it.b ? L.tx_b : L.tx_a));
     if (!it.b) {
-        bulk_hint(lk, blk, (unsigned)(f.eY + 72 * T), full, pol);
-        bulk_hint(lk + f.eZ, bzm + f.eZ, (unsigned)(72 * T), full, pol);
-        bulk_hint(lk + f.eT, btm + f.eT, (unsigned)(72 * T), full, pol);
+        bulk_hint(lk, blk, (unsigned)(f.eY + 72 * T), full, pol_a);
+        bulk_hint(lk + f.eZ, bzm + f.eZ, (unsigned)(72 * T), full, pol_a);
+        bulk_hint(lk + f.eT, btm + f.eT, (unsigned)(72 * T), full, pol_a);
     } else {
-        bulk_hint(lk + f.oX, blk + f.oX, (unsigned)(f.bytes - f.oX), full, pol);
-        bulk_hint(lk + f.oZ, bzm + f.oZ, (unsigned)(72 * T), full, pol);
-        bulk_hint(lk + f.oT, btm + f.oT, (unsigned)(72 * T), full, pol);
+        bulk_hint(lk + f.oX, blk + f.oX, (unsigned)(f.bytes - f.oX), full, pol_b);
+        bulk_hint(lk + f.oZ, bzm + f.oZ, (unsigned)(72 * T), full, pol_b);
+        bulk_hint(lk + f.oT, btm + f.oT, (unsigned)(72 * T), full, pol_b);
     }
     const CUtensorMap *mt = it.b ? &P.mid_tile : &P.in_tile;
     const CUtensorMap *mr = it.b ? &P.mid_row : &P.in_row;
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.in_row)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mid_tile)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mid_row)) : "memory");
-        const uint64_t pol = policy_evict_first();
+        const uint64_t pol_a = policy_evict_last(), pol_b = policy_evict_first();
         const unsigned need = (unsigned)(P.tps * P.tpt);  // team stores of one slice
         int known[4] = {-1, -1, -1, -1};  // slices seen complete (most recent four)
         int kn = 0;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
                 if (waited) asm volatile("fence.proxy.async.global;" ::: "memory");
             }
             slot[s] = q;
-            fs_issue(P, it, smem + s * L.bytes, full + s, pol);
+            fs_issue(P, it, smem + s * L.bytes, full + s, pol_a, pol_b);
         }
         // stop every consumer group: the next NS stages carry no item. After an
         // error a stage may still be busy; its group gives up by its own bounded
