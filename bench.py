@@ -455,7 +455,8 @@ def run_ours(args, rank, world, local):
     alu_peaks = {}
     try:
         alu_peaks = {"f64_tflops": round(weo.wilson_eo_alu_peak("f64") / 1e12, 3),
-                     "f32_tflops": round(weo.wilson_eo_alu_peak("f32") / 1e12, 2)}
+                     "f32_tflops": round(weo.wilson_eo_alu_peak("f32") / 1e12, 2),
+                     "l2_read_gbs": round(weo.wilson_eo_l2_peak() / 1e9, 1)}
     except Exception as exc:  # pragma: no cover
         alu_peaks = {"error": repr(exc)}
 

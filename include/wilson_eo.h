@@ -493,6 +493,15 @@ int wilson_eo_spinor_layout(long long half_volume, int nrhs, int elem_bytes, int
  * returns. Other precisions: WEO_ERR_ARG. */
 int wilson_eo_alu_peak(int prec, double *flops_per_s, void *stream);
 
+/* Measured read bandwidth from L2 into the SMs of the current GPU, in bytes/s:
+ * every SM streams a 48 MiB buffer (resident in L2 after a warm-up pass) with
+ * 16-byte L2-only loads, 40 passes, timed with CUDA events on `stream`. A
+ * measurement aid with no counterpart in the paper: the hopping kernels re-read
+ * neighbour spinors and links from L2 several times per site, and this is the
+ * second roofline they are reported against. Allocates and frees its buffer;
+ * synchronises with the stream before it returns. */
+int wilson_eo_l2_peak(double *bytes_per_s, void *stream);
+
 /* Release everything the handle owns (synchronises the device first).
  * NULL is accepted. */
 void wilson_eo_destroy(wilson_eo_t h);

@@ -86,6 +86,7 @@ def _load():
         "wilson_eo_solve_stats": (I, [P, IP, IP, IP, IP, ctypes.POINTER(D)]),
         "wilson_eo_solver_residual": (I, [P, I]),
         "wilson_eo_solver_restart": (I, [P, I]),
+        "wilson_eo_l2_peak": (I, [ctypes.POINTER(D), P]),
         "wilson_eo_set_tile_links": (I, [P, I]),
         "wilson_eo_get_tile_links": (I, [P, P]),
         "wilson_eo_spinor_layout": (I, [ctypes.c_longlong, I, I, I, P, P, P]),
@@ -357,6 +358,13 @@ def wilson_eo_alu_peak(prec="f64", stream=None):
     out = ctypes.c_double(0.0)
     _check(_load().wilson_eo_alu_peak(PREC.get(prec, -1), ctypes.byref(out), _stream(stream)),
            "wilson_eo_alu_peak")
+    return out.value
+
+
+def wilson_eo_l2_peak(stream=None):
+    """Measured L2 -> SM read bandwidth of the current GPU in bytes/s."""
+    out = ctypes.c_double(0.0)
+    _check(_load().wilson_eo_l2_peak(ctypes.byref(out), _stream(stream)), "wilson_eo_l2_peak")
     return out.value
 
 

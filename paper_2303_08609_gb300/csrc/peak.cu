@@ -78,9 +78,80 @@ static int fma_peak(double *flops, cudaStream_t s)
     return WEO_OK;
 }
 
+// ------------------------------------------------ L2 -> SM read bandwidth --
+// Every thread reads 16-byte words of an L2-resident buffer with L2-only loads
+// (ld.global.cg: no L1), grid-strided so each warp request is one contiguous
+// 512-byte range, for `passes` passes; the sum keeps the loads live.
+constexpr int kL2Threads = 512;
+constexpr int kL2BlocksPerSm = 4;
+
+__global__ void __launch_bounds__(kL2Threads) l2_read_kernel(const float4 *buf, long long n4, int passes)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    float acc = 0.f;
+    for (int p = 0; p < passes; ++p)
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc += v.x + v.y + v.z + v.w;
+        }
+    if (acc == 1234.5f) g_peak_sink = acc;  // the buffer holds zeros: never taken
+}
+
+static int l2_peak(double *bytes_per_s, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    WEO_CUDA(cudaGetDevice(&dev));
+    WEO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // 48 MiB: well inside the L2 of this GPU (129 MB), far beyond its L1s
+    const long long bytes = 48ll << 20, n4 = bytes / 16;
+    Buffer buf;
+    WEO_TRY(buf.ensure((size_t)bytes));
+    int st = WEO_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    do {
+        cudaError_t e = cudaMemsetAsync(buf.ptr, 0, (size_t)bytes, s);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) {
+            st = fail_cuda(e, "L2 probe set-up", __FILE__, __LINE__);
+            break;
+        }
+        const int grid = sms * kL2BlocksPerSm;
+        // warm: bring the buffer into L2
+        l2_read_kernel<<<grid, kL2Threads, 0, s>>>(static_cast<const float4 *>(buf.ptr), n4, 2);
+        const int passes = 40;
+        cudaEventRecord(e0, s);
+        l2_read_kernel<<<grid, kL2Threads, 0, s>>>(static_cast<const float4 *>(buf.ptr), n4, passes);
+        cudaEventRecord(e1, s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            st = fail_cuda(e, "L2 probe kernel", __FILE__, __LINE__);
+            break;
+        }
+        *bytes_per_s = (double)bytes * passes / (ms * 1e-3);
+    } while (false);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    buf.release();
+    return st;
+}
+
 }  // namespace weo
 
 using namespace weo;
+
+extern "C" int wilson_eo_l2_peak(double *bytes_per_s, void *stream)
+{
+    try {
+        if (!bytes_per_s) return set_error(WEO_ERR_ARG, "bytes_per_s is NULL");
+        return l2_peak(bytes_per_s, static_cast<cudaStream_t>(stream));
+    } catch (...) {
+        return set_error(WEO_ERR_OOM, "host exception in wilson_eo_l2_peak");
+    }
+}
 
 extern "C" int wilson_eo_alu_peak(int prec, double *flops_per_s, void *stream)
 {

@@ -16,3 +16,14 @@ def test_alu_peaks_are_plausible():
     # repeatable to a few percent
     again = weo.wilson_eo_alu_peak("f64")
     assert abs(again - f64) / f64 < 0.1
+
+
+def test_l2_read_bandwidth_is_plausible():
+    """The L2 -> SM read probe: above the HBM copy bandwidth's order of magnitude
+    floor and below any plausible on-chip rate, and repeatable."""
+    import paper_2303_08609_gb300 as weo
+
+    bw = weo.wilson_eo_l2_peak()
+    assert 1e12 < bw < 1e14
+    again = weo.wilson_eo_l2_peak()
+    assert abs(again - bw) / bw < 0.15
