@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tile-links", type=int, default=-1, metavar="N",
                     help="with --only-multi-rhs: hops over tiles with links in shared memory, N "
                          "right-hand sides per pass (0: off); default: autotuned")
+    ap.add_argument("--tile-rpt", type=int, default=1, metavar="R",
+                    help="with --tile-links: right-hand sides per thread sharing each link read (1, 2)")
     ap.add_argument("--dims", type=int, nargs=4, default=None,
                     help="lattice extents (default 32 32 32 64, the benchmark workload)")
     args = ap.parse_args()
@@ -679,13 +681,14 @@ def extras(U, psi, dev, stream):
         res[f"rhs_per_thread_{rb}"] = {"ms_per_step": round(ms, 4),
                                        "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
     weo.wilson_eo_set_launch(op.handle, 128, 1)
-    for nrl in (2, 4, 8):  # tiles with their links in shared memory, nrl RHS per pass
-        weo.wilson_eo_set_tile_links(op.handle, nrl)
+    for nrl, rpt in ((2, 1), (4, 1), (8, 1), (2, 2), (4, 2)):
+        # tiles with their links in shared memory: nrl thread groups, rpt RHS per thread
+        weo.wilson_eo_set_tile_links(op.handle, nrl, rpt)
         ms = timed(lambda: (weo.wilson_eo_apply(op.handle, y, x, 12, stream),
                             weo.wilson_eo_apply_dag(op.handle, z, y, 12, stream)), 50, stream)
-        res[f"tile_links_{nrl}"] = {"ms_per_step": round(ms, 4),
-                                    "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
-    weo.wilson_eo_set_tile_links(op.handle, 0)
+        res[f"tile_links_{nrl}x{rpt}"] = {"ms_per_step": round(ms, 4),
+                                          "gflops": round(12 * 2 * FLOP_PER_SITE * V / (ms * 1e-3) / 1e9, 1)}
+    weo.wilson_eo_set_tile_links(op.handle, 0, 1)
     t, rb, tms = weo.wilson_eo_tune(op.handle, 12, stream)
     lanes = weo.wilson_eo_get_launch(op.handle)[2]
     res["tuned"] = {"threads": t, "rhs_per_thread": rb, "rhs_lanes": lanes,
@@ -1061,7 +1064,7 @@ def multi_rhs_only(args, local):
     y, z = torch.empty_like(x), torch.empty_like(x)
     stream = torch.cuda.current_stream(dev)
     if args.tile_links >= 0:
-        weo.wilson_eo_set_tile_links(op.handle, args.tile_links)
+        weo.wilson_eo_set_tile_links(op.handle, args.tile_links, args.tile_rpt)
     else:
         weo.wilson_eo_tune(op.handle, n, stream)
     t, rb, lanes = weo.wilson_eo_get_launch(op.handle)

@@ -404,18 +404,20 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes);
 
 /* Several right-hand sides with each tile's links loaded once (the batching
  * pattern of the multi-RHS hop; Table 1's tiling sweep is the paper's
- * analogue, Sec. 4): a CTA of 256 threads takes a tile of 256 / rhs_per_pass
+ * analogue, Sec. 4): a CTA of 256 threads takes a tile of 256 / groups
  * consecutive output sites, copies the eight links of every tile site into
- * shared memory (as FP32, 576 bytes per site), and then passes over the tile
- * rhs_per_pass right-hand sides at a time until all nrhs are done; spinors are
- * read from global memory. rhs_per_pass 2, 4 or 8 turns it on for the
- * handle's FP32 or 16-bit hops whenever nrhs >= 2 (and sets one right-hand
- * side per thread); 0 (default) turns it off. WEO_ERR_ARG for other values,
+ * shared memory (as FP32, 576 bytes per site), and then passes over the tile,
+ * its `groups` thread groups each taking rhs_per_thread right-hand sides per
+ * pass (1, or 2 sharing every link read from shared memory; 2 is used when
+ * nrhs >= 2 groups), until all nrhs are done; spinors are read from global
+ * memory. groups 2, 4 or 8 turns it on for the handle's FP32 or 16-bit hops
+ * whenever nrhs >= 2 (and sets one right-hand side per thread for the other
+ * kernels); 0 (default) turns it off. WEO_ERR_ARG for other values,
  * WEO_ERR_UNSUPPORTED on an FP64 handle. wilson_eo_tune times these
  * configurations too. */
-int wilson_eo_set_tile_links(wilson_eo_t h, int rhs_per_pass);
-/* The handle's current rhs_per_pass (0 = off). */
-int wilson_eo_get_tile_links(wilson_eo_t h, int *rhs_per_pass);
+int wilson_eo_set_tile_links(wilson_eo_t h, int groups, int rhs_per_thread);
+/* The handle's current groups (0 = off) and right-hand sides per thread. */
+int wilson_eo_get_tile_links(wilson_eo_t h, int *groups, int *rhs_per_thread);
 
 /* M_eo in_e (dag = 0) or M_eo^dag in_e (dag = 1) in float-float arithmetic:
  * every real is carried as an unevaluated sum hi + lo of two floats (about 48

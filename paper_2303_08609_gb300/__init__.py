@@ -87,8 +87,8 @@ def _load():
         "wilson_eo_solver_residual": (I, [P, I]),
         "wilson_eo_solver_restart": (I, [P, I]),
         "wilson_eo_l2_peak": (I, [ctypes.POINTER(D), P]),
-        "wilson_eo_set_tile_links": (I, [P, I]),
-        "wilson_eo_get_tile_links": (I, [P, P]),
+        "wilson_eo_set_tile_links": (I, [P, I, I]),
+        "wilson_eo_get_tile_links": (I, [P, P, P]),
         "wilson_eo_spinor_layout": (I, [ctypes.c_longlong, I, I, I, P, P, P]),
         "wilson_eo_apply_ff64": (I, [P, P, P, I, I, P]),
         "wilson_eo_apply_batch": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -444,16 +444,20 @@ def wilson_eo_solver_residual(h, mode):
     _check(_load().wilson_eo_solver_residual(h, int(mode)), "wilson_eo_solver_residual")
 
 
-def wilson_eo_set_tile_links(h, rhs_per_pass):
-    """Multi-RHS hops over tiles whose links sit in shared memory, rhs_per_pass
-    (2, 4, 8) right-hand sides at a time; 0 turns it off."""
-    _check(_load().wilson_eo_set_tile_links(h, int(rhs_per_pass)), "wilson_eo_set_tile_links")
+def wilson_eo_set_tile_links(h, groups, rhs_per_thread=1):
+    """Multi-RHS hops over tiles whose links sit in shared memory: ``groups``
+    (2, 4, 8) thread groups per tile, each taking ``rhs_per_thread`` (1, 2)
+    right-hand sides per pass; groups = 0 turns it off."""
+    _check(_load().wilson_eo_set_tile_links(h, int(groups), int(rhs_per_thread)),
+           "wilson_eo_set_tile_links")
 
 
 def wilson_eo_get_tile_links(h):
-    n = ctypes.c_int(0)
-    _check(_load().wilson_eo_get_tile_links(h, ctypes.byref(n)), "wilson_eo_get_tile_links")
-    return n.value
+    """(groups, rhs_per_thread) of the handle's tile-shared-link hops."""
+    n, r = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_load().wilson_eo_get_tile_links(h, ctypes.byref(n), ctypes.byref(r)),
+           "wilson_eo_get_tile_links")
+    return n.value, r.value
 
 
 def wilson_eo_spinor_layout(dst, src, to_planar=True, stream=None):

@@ -387,22 +387,26 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
     return WEO_OK;
 }
 
-int wilson_eo_set_tile_links(wilson_eo_t h, int rhs_per_pass)
+int wilson_eo_set_tile_links(wilson_eo_t h, int groups, int rhs_per_thread)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
-    if (rhs_per_pass != 0 && rhs_per_pass != 2 && rhs_per_pass != 4 && rhs_per_pass != 8)
-        return set_error(WEO_ERR_ARG, "rhs_per_pass must be 0, 2, 4 or 8");
-    if (rhs_per_pass && h->prec == WEO_F64)
+    if (groups != 0 && groups != 2 && groups != 4 && groups != 8)
+        return set_error(WEO_ERR_ARG, "groups must be 0, 2, 4 or 8");
+    if (rhs_per_thread != 1 && rhs_per_thread != 2)
+        return set_error(WEO_ERR_ARG, "rhs_per_thread must be 1 or 2");
+    if (groups && h->prec == WEO_F64)
         return set_error(WEO_ERR_UNSUPPORTED, "tile-shared links need an FP32 or 16-bit handle");
-    h->cfg[h->prec].tile_links = rhs_per_pass;
-    if (rhs_per_pass) h->cfg[h->prec].rhs_block = 1;
+    h->cfg[h->prec].tile_links = groups;
+    h->cfg[h->prec].tile_rhs_per_thread = rhs_per_thread;
+    if (groups) h->cfg[h->prec].rhs_block = 1;
     return WEO_OK;
 }
 
-int wilson_eo_get_tile_links(wilson_eo_t h, int *rhs_per_pass)
+int wilson_eo_get_tile_links(wilson_eo_t h, int *groups, int *rhs_per_thread)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
-    if (rhs_per_pass) *rhs_per_pass = h->cfg[h->prec].tile_links;
+    if (groups) *groups = h->cfg[h->prec].tile_links;
+    if (rhs_per_thread) *rhs_per_thread = h->cfg[h->prec].tile_rhs_per_thread;
     return WEO_OK;
 }
 

@@ -268,8 +268,9 @@ __global__ void __launch_bounds__(256, 4) hop_kernel_lanes(const HopParams p)
 // copies the eight links of every tile site -- U_mu(x) and U_mu(x - mu) for the
 // backward hop -- into shared memory (converted to FP32 complex, [8][9][T],
 // 576 T bytes), then its NRL groups of T threads take the right-hand sides
-// rhs0 = 0 .. NRL-1 and step by NRL, one (site, right-hand side) per thread,
-// with the spinors read from global memory as in hop_kernel. A link leaves
+// rhs0 = 0 .. NRL-1 and step by NRL, one (site, right-hand side) per thread --
+// or RP right-hand sides per thread sharing each link read from shared memory
+// -- with the spinors read from global memory as in hop_kernel. A link leaves
 // global memory once per tile instead of once per right-hand-side block.
 
 // compact indices of the 8 neighbours of site i (order: +x, -x, +y, -y, +z,
@@ -298,9 +299,10 @@ __device__ __forceinline__ void site_neighbours(const HopParams &p, int i, int n
 
 // one hopping direction with the link from shared memory (9 complex at
 // stride T from lk)
-template <class SIn, int MU, bool FWD, int S0>
-__device__ __forceinline__ void hop_dir_shared(cx<float> (&acc)[12], const HopParams &p, int nb,
-                                               const float2 *lk, int T, int rhs)
+// (RP right-hand sides rhs, rhs + step, ... share the link's registers)
+template <class SIn, int MU, bool FWD, int S0, int RP>
+__device__ __forceinline__ void hop_dir_shared(cx<float> (&acc)[RP][12], const HopParams &p, int nb,
+                                               const float2 *lk, int T, int rhs, int step)
 {
     constexpr int S = FWD ? S0 : -S0;
     cx<float> U[3][3];
@@ -309,28 +311,32 @@ __device__ __forceinline__ void hop_dir_shared(cx<float> (&acc)[12], const HopPa
         const float2 u = lk[k * T];
         U[k / 3][k % 3] = {u.x, u.y};
     }
-    cx<float> v[12];
-    SIn::load(static_cast<const char *>(p.in) + rhs * p.in_stride, p.vh, nb, v);
-    cx<float> h[2][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
-    cx<float> w[2][3];
+    for (int r = 0; r < RP; ++r) {
+        if (RP > 1 && rhs + r * step >= p.nrhs) break;
+        cx<float> v[12];
+        SIn::load(static_cast<const char *>(p.in) + (rhs + r * step) * p.in_stride, p.vh, nb, v);
+        cx<float> h[2][3];
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+        for (int c = 0; c < 3; ++c) project<MU, S>(v[c], v[3 + c], v[6 + c], v[9 + c], h[0][c], h[1][c]);
+        cx<float> w[2][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            cx<float> z = {0.f, 0.f};
+        for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[sp][b], z) : cfmaconj(U[b][a], h[sp][b], z);
-            w[sp][a] = z;
-        }
+            for (int a = 0; a < 3; ++a) {
+                cx<float> z = {0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-        reconstruct<MU, S>(acc[c], acc[3 + c], acc[6 + c], acc[9 + c], w[0][c], w[1][c]);
+                for (int b = 0; b < 3; ++b) z = FWD ? cfma(U[a][b], h[sp][b], z) : cfmaconj(U[b][a], h[sp][b], z);
+                w[sp][a] = z;
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            reconstruct<MU, S>(acc[r][c], acc[r][3 + c], acc[r][6 + c], acc[r][9 + c], w[0][c], w[1][c]);
+    }
 }
 
-template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL>
-__global__ void __launch_bounds__(256, 3) hop_kernel_tile_links(const HopParams p)
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL, int RP = 1>
+__global__ void __launch_bounds__(256, RP == 1 ? 3 : 2) hop_kernel_tile_links(const HopParams p)
 {
     constexpr int T = 256 / NRL;
     extern __shared__ __align__(16) float2 lk_sm[];  // [8 directions][9 complex][T]
@@ -361,31 +367,39 @@ __global__ void __launch_bounds__(256, 3) hop_kernel_tile_links(const HopParams 
     if (i >= p.vh) return;
     constexpr int S0 = Dag ? -1 : 1;
     const float2 *lk = lk_sm + s;
-    for (int r = rl; r < p.nrhs; r += NRL) {
+    // each thread takes right-hand sides r, r + NRL, ..., RP of them per pass
+    for (int r = rl; r < p.nrhs; r += NRL * RP) {
         int nb[8];
         site_neighbours(p, i, nb);
-        cx<float> acc[12];
+        cx<float> acc[RP][12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
-        hop_dir_shared<SIn, 0, true, S0>(acc, p, nb[0], lk + 0 * 9 * T, T, r);
-        hop_dir_shared<SIn, 0, false, S0>(acc, p, nb[1], lk + 1 * 9 * T, T, r);
-        hop_dir_shared<SIn, 1, true, S0>(acc, p, nb[2], lk + 2 * 9 * T, T, r);
-        hop_dir_shared<SIn, 1, false, S0>(acc, p, nb[3], lk + 3 * 9 * T, T, r);
-        hop_dir_shared<SIn, 2, true, S0>(acc, p, nb[4], lk + 4 * 9 * T, T, r);
-        hop_dir_shared<SIn, 2, false, S0>(acc, p, nb[5], lk + 5 * 9 * T, T, r);
-        hop_dir_shared<SIn, 3, true, S0>(acc, p, nb[6], lk + 6 * 9 * T, T, r);
-        hop_dir_shared<SIn, 3, false, S0>(acc, p, nb[7], lk + 7 * 9 * T, T, r);
-        if (Axpy) {
-            cx<float> xv[12];
-            SX::load(static_cast<const char *>(p.x) + r * p.x_stride, p.vh, i, xv);
-            const float a = float(p.a);
+        for (int q = 0; q < RP; ++q)
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                acc[k].r = fmaf(a, acc[k].r, xv[k].r);
-                acc[k].i = fmaf(a, acc[k].i, xv[k].i);
+            for (int k = 0; k < 12; ++k) acc[q][k] = {0.f, 0.f};
+        hop_dir_shared<SIn, 0, true, S0, RP>(acc, p, nb[0], lk + 0 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 0, false, S0, RP>(acc, p, nb[1], lk + 1 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 1, true, S0, RP>(acc, p, nb[2], lk + 2 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 1, false, S0, RP>(acc, p, nb[3], lk + 3 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 2, true, S0, RP>(acc, p, nb[4], lk + 4 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 2, false, S0, RP>(acc, p, nb[5], lk + 5 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 3, true, S0, RP>(acc, p, nb[6], lk + 6 * 9 * T, T, r, NRL);
+        hop_dir_shared<SIn, 3, false, S0, RP>(acc, p, nb[7], lk + 7 * 9 * T, T, r, NRL);
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+            const int rq = r + q * NRL;
+            if (RP > 1 && rq >= p.nrhs) break;
+            if (Axpy) {
+                cx<float> xv[12];
+                SX::load(static_cast<const char *>(p.x) + rq * p.x_stride, p.vh, i, xv);
+                const float a = float(p.a);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    acc[q][k].r = fmaf(a, acc[q][k].r, xv[k].r);
+                    acc[q][k].i = fmaf(a, acc[q][k].i, xv[k].i);
+                }
             }
+            SOut::store(static_cast<char *>(p.out) + rq * p.out_stride, p.vh, i, acc[q]);
         }
-        SOut::store(static_cast<char *>(p.out) + r * p.out_stride, p.vh, i, acc);
     }
 }
 

@@ -77,6 +77,7 @@ struct LaunchCfg {
     int staged = 0;      // FP32 18-real, one RHS: operands staged in shared memory by TMA
     int tile_links = 0;  // several RHS: right-hand sides per pass over a tile whose links
                          // sit in shared memory (2, 4 or 8; 0 = off)
+    int tile_rhs_per_thread = 1;  // ... and right-hand sides per thread sharing each link read (1, 2)
 };
 
 struct Profiler;

@@ -19,12 +19,12 @@ int launch_lanes(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
     return WEO_OK;
 }
 
-template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL>
+template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int NRL, int RP = 1>
 int launch_tile_links(const HopParams &p, cudaStream_t s)
 {
     constexpr int T = 256 / NRL;
     const size_t smem = (size_t)576 * T;
-    auto kern = hop_kernel_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, NRL>;
+    auto kern = hop_kernel_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, NRL, RP>;
     if (smem > 48 * 1024) {
         static bool attr_set = false;  // per instance; idempotent if two threads race
         if (!attr_set) {
@@ -43,6 +43,13 @@ int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
     if constexpr (R == 1 && sizeof(typename SOut::real) == 4) {
         // several right-hand sides over tiles whose links sit in shared memory
         if (cfg.tile_links && p.nrhs >= 2) {
+            // 2 right-hand sides per thread (sharing each link read) when asked
+            // for and there are enough of them to fill a pass
+            if (cfg.tile_rhs_per_thread == 2 && p.nrhs >= 2 * cfg.tile_links) {
+                if (cfg.tile_links == 8) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 8, 2>(p, s);
+                if (cfg.tile_links == 4) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 4, 2>(p, s);
+                return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 2, 2>(p, s);
+            }
             if (cfg.tile_links == 8) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 8>(p, s);
             if (cfg.tile_links == 4) return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 4>(p, s);
             return launch_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, 2>(p, s);

@@ -168,8 +168,8 @@ def test_spinor_layout_rejects_bad_arguments_before_the_device(lib):
 
 
 def test_tile_links_rejects_null(lib):
-    assert lib.wilson_eo_set_tile_links(None, 4) == -1
-    assert lib.wilson_eo_get_tile_links(None, None) == -1
+    assert lib.wilson_eo_set_tile_links(None, 4, 1) == -1
+    assert lib.wilson_eo_get_tile_links(None, None, None) == -1
 
 
 def test_l2_peak_rejects_null(lib):
