@@ -754,6 +754,16 @@ def extras(U, psi, dev, stream):
                           for o, yy, xx in zip(ops, ys, xs)], 50, stream)
     out["batch_16_24_32_f32"] = {"ms_one_launch": round(ms_b, 4), "ms_separate_applies": round(ms_s, 4),
                                  "gflops_one_launch": round(FLOP_PER_SITE * sites / (ms_b * 1e-3) / 1e9, 1)}
+    # the same three lattices with 4 right-hand sides each: one launch (tiles whose
+    # links sit in shared memory) against one multi-RHS apply per lattice
+    xs4 = [torch.cat([xx.unsqueeze(0)] * 4) for xx in xs]
+    ys4 = [torch.empty_like(xx) for xx in xs4]
+    ms_b4 = timed(lambda: weo.wilson_eo_apply_batch_rhs(hs, ys4, xs4, [4, 4, 4], False, stream), 20, stream)
+    ms_s4 = timed(lambda: [weo.wilson_eo_apply(o.handle, yy, xx, 4, stream)
+                           for o, yy, xx in zip(ops, ys4, xs4)], 20, stream)
+    out["batch_16_24_32_f32_4rhs"] = {"ms_one_launch": round(ms_b4, 4), "ms_separate_applies": round(ms_s4, 4),
+                                      "gflops_one_launch": round(4 * FLOP_PER_SITE * sites / (ms_b4 * 1e-3) / 1e9, 1)}
+    del xs4, ys4
     for o in ops:
         o.close()
     return out

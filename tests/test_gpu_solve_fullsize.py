@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import gen
-from gpu_util import from_planar, rel_l2, to_planar
+from gpu_util import TOL, from_planar, rel_l2, to_planar
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -36,18 +36,24 @@ def oracle_relres(oracle_lib, U, kappa, x, b, dims):
     return float(np.linalg.norm(b - ax) / np.linalg.norm(b))
 
 
-def test_solve_48x48x48x96_mixed_and_plain(weo, oracle_lib):
+@pytest.fixture(scope="module")
+def fields_48x96():
+    """The solve workload's inputs: 48^3 x 96, exp(i 0.4 H) links (seed 0),
+    Gaussian b (seed 1)."""
+    dims = (48, 48, 48, 96)
+    return dims, gen.gauge_field(dims, "smooth", seed=0, eps=0.4), gen.gaussian_spinor(dims, seed=1)[0]
+
+
+def test_solve_48x48x48x96_mixed_and_plain(weo, oracle_lib, fields_48x96):
     """48^3 x 96, kappa = 0.135, exp(i 0.4 H) links (seed 0), Gaussian b (seed 1):
     the FP16-storage mixed solve (12-real links, float-float reliable updates)
     and the plain FP64 CG, each x checked by the oracle; the two solutions agree
     to what the condition number allows."""
     import torch
 
-    dims = (48, 48, 48, 96)
+    dims, U, b = fields_48x96
     kappa = 0.135
     oracle_lib.set_threads(os.cpu_count() or 1)
-    U = gen.gauge_field(dims, "smooth", seed=0, eps=0.4)
-    b = gen.gaussian_spinor(dims, seed=1)[0]
     Ud = torch.from_numpy(U).cuda()
     bd = torch.from_numpy(to_planar(b)).cuda()
     xs = {}
@@ -89,3 +95,34 @@ def test_solve_twelve_point_sources_32x32x32x64(weo, oracle_lib, fields_32x64):
         rr = oracle_relres(oracle_lib, U, kappa, xg[r], b[r], dims)
         assert rr <= BAR, (r, rr)
         assert abs(rr - info["true_relres"][r]) <= 1e-3 * rr, (r, rr, info["true_relres"][r])
+
+
+@pytest.mark.parametrize("prec,fmt,path", [("f32", 18, "staged"), ("f16", 12, "plain"), ("bf16", 12, "plain")])
+def test_meo_whole_lattice_48x48x48x96(weo, oracle_lib, fields_48x96, prec, fmt, path):
+    """The largest workload: M_eo and M_eo^dag of b on all 5,308,416 even sites
+    of 48^3 x 96 (kappa = 0.135) against the oracle, relative L2 within the
+    storage precision's bar and every site within 10x of it (relative to the
+    RMS site norm)."""
+    import torch
+
+    dims, U, b = fields_48x96
+    kappa = 0.135
+    oracle_lib.set_threads(os.cpu_count() or 1)
+    op = weo.WilsonEO(dims, kappa, torch.from_numpy(U).cuda(), prec=prec, linkfmt=fmt)
+    if path == "staged":
+        weo.wilson_eo_set_staging(op.handle, True)
+        assert weo.wilson_eo_get_staging(op.handle)["staged"]
+    x = torch.from_numpy(to_planar(b).astype(np.complex64)).cuda()
+    for dag in (False, True):
+        y = op.apply(x, dag=dag)
+        weo.wilson_eo_check(op.handle)
+        got = from_planar(y.cpu().numpy())
+        del y
+        want = (oracle_lib.meo_dag if dag else oracle_lib.meo)(U, kappa, b, dims)
+        err = rel_l2(got, want)
+        d = np.linalg.norm((got - want).reshape(-1, 12), axis=1)
+        rms = np.sqrt(np.mean(np.linalg.norm(want.reshape(-1, 12), axis=1) ** 2))
+        assert err <= TOL[prec], err
+        assert d.max() / rms <= 10 * TOL[prec], d.max() / rms
+    op.close()
+    torch.cuda.empty_cache()
