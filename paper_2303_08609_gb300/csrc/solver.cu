@@ -656,7 +656,19 @@ static int solve_impl(wilson_eo_s *h, double tol, int maxiter, int mixed, int *i
     for (int r = 0; r < R; ++r)
         if (bb[r] == 0.0)
             WEO_CUDA(cudaMemsetAsync(static_cast<char *>(S->x64.ptr) + r * v64, 0, v64, s));
-    WEO_TRY(update_residual(h, S, *ghi, ff, active, target));
+    // a zero initial guess needs no operator application: r = b
+    k_norm2<double2><<<grid, kRedThreads, 0, s>>>((const double2 *)S->x64.ptr, n, sc, 0);
+    WEO_CUDA(cudaGetLastError());
+    WEO_TRY(read_scalars(S));
+    bool zero_guess = true;
+    for (int r = 0; r < R; ++r)
+        if (S->host[r].red != 0.0) zero_guess = false;
+    if (zero_guess) {
+        WEO_CUDA(cudaMemcpyAsync(S->r64.ptr, S->b64.ptr, b64, cudaMemcpyDeviceToDevice, s));
+        for (int r = 0; r < R; ++r) S->host[r].red = bb[r];
+    } else {
+        WEO_TRY(update_residual(h, S, *ghi, ff, active, target));
+    }
     int n_active = R;
     auto retire = [&](int r) -> int {  // right-hand side r has converged
         active[r] = 0;
