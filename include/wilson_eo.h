@@ -402,6 +402,17 @@ int wilson_eo_set_launch(wilson_eo_t h, int threads, int rhs_block, int order);
  * on an FP64 handle. */
 int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes);
 
+/* Site order of the one-site-per-thread hopping kernels (every precision):
+ * blocked 0 (default) gives each CTA consecutive parity indices, i.e. whole
+ * rows of one (z, t) plane; blocked 1 gives each CTA of 8 Lx/2 threads the
+ * rows (y0 + dy, z0 + dz, t0 + dt), dy, dz, dt in {0, 1}, so that half of its
+ * y, z and t neighbour rows are rows it reads anyway and come from L1 rather
+ * than L2 (Sec. 3.2 blocks sites in x and y for the same reason). Used when
+ * 64 <= 8 Lx/2 <= 256; the CTA size then replaces wilson_eo_set_launch's
+ * `threads`. The results do not depend on it. WEO_ERR_ARG for other values.
+ * wilson_eo_tune times it too. */
+int wilson_eo_set_site_blocks(wilson_eo_t h, int blocked);
+
 /* Several right-hand sides with each tile's links loaded once (the batching
  * pattern of the multi-RHS hop; Table 1's tiling sweep is the paper's
  * analogue, Sec. 4): a CTA of 256 threads takes a tile of 256 / groups

@@ -88,6 +88,7 @@ def _load():
         "wilson_eo_solver_restart": (I, [P, I]),
         "wilson_eo_l2_peak": (I, [ctypes.POINTER(D), P]),
         "wilson_eo_set_tile_links": (I, [P, I, I]),
+        "wilson_eo_set_site_blocks": (I, [P, I]),
         "wilson_eo_get_tile_links": (I, [P, P, P]),
         "wilson_eo_spinor_layout": (I, [ctypes.c_longlong, I, I, I, P, P, P]),
         "wilson_eo_apply_ff64": (I, [P, P, P, I, I, P]),
@@ -442,6 +443,11 @@ def wilson_eo_solver_residual(h, mode):
     """True residuals of reliable updates: 1 float-float (FP64 confirms
     convergence), 0 native FP64."""
     _check(_load().wilson_eo_solver_residual(h, int(mode)), "wilson_eo_solver_residual")
+
+
+def wilson_eo_set_site_blocks(h, blocked=True):
+    """One-site-per-thread hops: CTAs take 2x2x2 blocks of rows in (y, z, t)."""
+    _check(_load().wilson_eo_set_site_blocks(h, int(bool(blocked))), "wilson_eo_set_site_blocks")
 
 
 def wilson_eo_set_tile_links(h, groups, rhs_per_thread=1):

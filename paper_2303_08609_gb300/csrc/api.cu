@@ -387,6 +387,14 @@ int wilson_eo_set_rhs_lanes(wilson_eo_t h, int lanes)
     return WEO_OK;
 }
 
+int wilson_eo_set_site_blocks(wilson_eo_t h, int blocked)
+{
+    if (!h) return set_error(WEO_ERR_ARG, "NULL handle");
+    if (blocked != 0 && blocked != 1) return set_error(WEO_ERR_ARG, "blocked must be 0 or 1");
+    for (auto &c : h->cfg) c.blocked = blocked;
+    return WEO_OK;
+}
+
 int wilson_eo_set_tile_links(wilson_eo_t h, int groups, int rhs_per_thread)
 {
     if (!h) return set_error(WEO_ERR_ARG, "NULL handle");

@@ -3,14 +3,14 @@
 // per CTA and (FP32 / 16-bit handles with several right-hand sides) 1, 2 or 4
 // right-hand sides per thread, or two right-hand sides on neighbouring lanes,
 // or tiles whose links sit in shared memory for 2, 4 or 8 right-hand sides at
-// a time;
+// a time, or CTAs over 2x2x2 blocks of rows;
 // and, for FP32 / 16-bit handles, the fused single-launch algorithm with a
 // lookahead of 4 or 8 t-slices and 128 or 256 threads per CTA; for FP32 18-real
 // handles the fused staged launch with a lookahead of 2 or 4. Results are
 // cached per process, keyed by (GPU name, extents, precision, link format,
 // nrhs), and optionally in a text file named by the environment variable
-// WILSON_EO_TUNE_CACHE (one "v6 key algo threads rhs_block lanes lookahead ms
-// staged tile_links tile_rpt" line each; v3 to v5 lines are still read).
+// WILSON_EO_TUNE_CACHE (one "v7 key algo threads rhs_block lanes lookahead ms
+// staged tile_links tile_rpt blocked" line each; v3 to v6 lines are still read).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -31,6 +31,7 @@ struct TuneEntry {
     int staged = 0;  // FP32 18-real hops through the TMA-staged kernel
     int tile_links = 0;  // several RHS over tiles with links in shared memory
     int tile_rpt = 1;    // ... right-hand sides per thread
+    int blocked = 0;     // one-site-per-thread hops over 2x2x2 blocks of rows
 };
 
 static std::mutex g_tune_mutex;
@@ -66,7 +67,9 @@ static void load_tune_file()
     char line[640], key[400];
     while (fgets(line, sizeof(line), f)) {
         TuneEntry e;
-        if (sscanf(line, "v6 %399s %d %d %d %d %d %lf %d %d %d", key, &e.algo, &e.threads, &e.rhs_block,
+        if (sscanf(line, "v7 %399s %d %d %d %d %d %lf %d %d %d %d", key, &e.algo, &e.threads, &e.rhs_block,
+                   &e.lanes, &e.lookahead, &e.ms, &e.staged, &e.tile_links, &e.tile_rpt, &e.blocked) == 11 ||
+            sscanf(line, "v6 %399s %d %d %d %d %d %lf %d %d %d", key, &e.algo, &e.threads, &e.rhs_block,
                    &e.lanes, &e.lookahead, &e.ms, &e.staged, &e.tile_links, &e.tile_rpt) == 10 ||
             sscanf(line, "v5 %399s %d %d %d %d %d %lf %d %d", key, &e.algo, &e.threads, &e.rhs_block,
                    &e.lanes, &e.lookahead, &e.ms, &e.staged, &e.tile_links) == 9 ||
@@ -85,8 +88,8 @@ static void append_tune_file(const std::string &key, const TuneEntry &e)
     if (!path || !*path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "v6 %s %d %d %d %d %d %.6f %d %d %d\n", key.c_str(), e.algo, e.threads, e.rhs_block,
-            e.lanes, e.lookahead, e.ms, e.staged, e.tile_links, e.tile_rpt);
+    fprintf(f, "v7 %s %d %d %d %d %d %.6f %d %d %d %d\n", key.c_str(), e.algo, e.threads, e.rhs_block,
+            e.lanes, e.lookahead, e.ms, e.staged, e.tile_links, e.tile_rpt, e.blocked);
     fclose(f);
 }
 
@@ -102,6 +105,7 @@ static int apply_entry(wilson_eo_s *h, const TuneEntry &e, cudaStream_t s)
         h->cfg[h->prec].lanes = e.lanes;
         h->cfg[h->prec].tile_links = e.tile_links;
         h->cfg[h->prec].tile_rhs_per_thread = e.tile_rpt;
+        h->cfg[h->prec].blocked = e.blocked;
     }
     if (h->prec == WEO_F32) {
         h->cfg[WEO_F32].staged = e.staged;
@@ -153,7 +157,7 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
     Profiler *saved_prof = h->prof;
     h->prof = nullptr;
     TuneEntry best = {saved_algo, saved.threads, saved.rhs_block, saved.lanes, saved_la, 1e30, saved.staged,
-                      saved.tile_links, saved.tile_rhs_per_thread};
+                      saved.tile_links, saved.tile_rhs_per_thread, saved.blocked};
     std::vector<TuneEntry> cands;
     for (int threads : {64, 128, 192, 256}) {
         for (int r : rb) cands.push_back({0, threads, r, 1, 0, 0.0});
@@ -166,6 +170,10 @@ int tune_handle(wilson_eo_s *h, int nrhs, cudaStream_t s, int *threads_out, int 
         cands.push_back({0, 128, 1, 1, 0, 0.0, 1});
     if (fstaged_eligible(h))
         for (int la : {2, 4}) cands.push_back({2, 128, 1, 1, la, 0.0});
+    if (8 * (h->dims[0] / 2) >= 64 && 8 * (h->dims[0] / 2) <= 256) {
+        cands.push_back({0, 128, 1, 1, 0, 0.0, 0, 0, 1, 1});  // blocked site order, one RHS per thread
+        if (h->prec != WEO_F64 && nrhs >= 2) cands.push_back({0, 128, 2, 1, 0, 0.0, 0, 0, 1, 1});
+    }
     if (h->prec != WEO_F64 && nrhs >= 2)
         for (int n : {2, 4, 8}) {
             if (n <= 2 * nrhs) cands.push_back({0, 256, 1, 1, 0, 0.0, 0, n, 1});

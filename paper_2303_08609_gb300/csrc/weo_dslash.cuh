@@ -42,6 +42,7 @@ struct HopParams {
     long long gauge_pb;
     double a;              // axpy coefficient
     int reverse;           // walk the sites from the top (blocks in reverse order)
+    int blocked;           // CTAs take 2x2x2 blocks of rows in (y, z, t) (blockDim = 8 Lx/2)
 };
 
 // h = psi_up - S A_mu psi_dn for one colour
@@ -221,13 +222,28 @@ __device__ __forceinline__ void block_coords(const HopParams &p, int nrb, int &s
     site_block = p.reverse ? nsb - 1 - sb : sb;
 }
 
+// Output site of thread t in site block b. Default: consecutive compact
+// indices (a CTA covers whole rows of one (z, t) plane). Blocked: a CTA of
+// 8 Lx/2 threads covers the rows (y0 + dy, z0 + dz, t0 + dt), dy, dz, dt in
+// {0, 1}, so half of its y, z and t neighbour rows are its own input rows
+// and reach it through L1 instead of L2 (all extents are even, so the blocks
+// tile the lattice exactly).
+__device__ __forceinline__ int site_of(const HopParams &p, int b, int t)
+{
+    if (!p.blocked) return b * (int)blockDim.x + t;
+    const int hy = p.ly >> 1, hz = p.lz >> 1;
+    const int y0 = 2 * (b % hy), z0 = 2 * ((b / hy) % hz), t0 = 2 * (b / (hy * hz));
+    const int row = t / p.lxh, xh = t - row * p.lxh;
+    return (((t0 + (row >> 2)) * p.lz + z0 + ((row >> 1) & 1)) * p.ly + y0 + (row & 1)) * p.lxh + xh;
+}
+
 // One output site per thread.
 template <class SIn, class SOut, class SX, class Lk, bool Dag, bool Axpy, int R>
 __global__ void __launch_bounds__(256) hop_kernel(const HopParams p)
 {
     int b, rb;
     block_coords(p, (p.nrhs + R - 1) / R, b, rb);
-    const int i = b * blockDim.x + threadIdx.x;
+    const int i = site_of(p, b, threadIdx.x);
     if (i >= p.vh) return;
     hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, rb * R);
 }
@@ -242,7 +258,7 @@ __global__ void __launch_bounds__(256, 4) hop_kernel_occ(const HopParams p)
 {
     int b, rb;
     block_coords(p, (p.nrhs + R - 1) / R, b, rb);
-    const int i = b * blockDim.x + threadIdx.x;
+    const int i = site_of(p, b, threadIdx.x);
     if (i >= p.vh) return;
     hop_site<SIn, SOut, SX, Lk, Dag, Axpy, R>(p, i, rb * R);
 }

@@ -78,6 +78,7 @@ struct LaunchCfg {
     int tile_links = 0;  // several RHS: right-hand sides per pass over a tile whose links
                          // sit in shared memory (2, 4 or 8; 0 = off)
     int tile_rhs_per_thread = 1;  // ... and right-hand sides per thread sharing each link read (1, 2)
+    int blocked = 0;     // one-site-per-thread hops: CTAs take 2x2x2 blocks of rows (y, z, t)
 };
 
 struct Profiler;

@@ -62,14 +62,20 @@ int launch_instance(const HopParams &p, const LaunchCfg &cfg, cudaStream_t s)
         if (nl == 4) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 4>(p, cfg, s);
         if (nl == 2) return launch_lanes<SIn, SOut, SX, Lk, Dag, Axpy, 2>(p, cfg, s);
     }
-    const int threads = cfg.threads;
-    dim3 grid((unsigned)(((p.vh + threads - 1) / threads) * ((p.nrhs + R - 1) / R)));
+    // blocked site order: CTAs of 8 Lx/2 threads, one per 2x2x2 block of rows
+    const bool blocked = cfg.blocked && 8 * p.lxh >= 64 && 8 * p.lxh <= 256;
+    const int threads = blocked ? 8 * p.lxh : cfg.threads;
+    const long long site_blocks = blocked ? (long long)(p.ly / 2) * (p.lz / 2) * (p.lt / 2)
+                                          : (p.vh + threads - 1) / threads;
+    HopParams q = p;
+    q.blocked = blocked ? 1 : 0;
+    dim3 grid((unsigned)(site_blocks * ((p.nrhs + R - 1) / R)));
     // the 64-register cap pays for 18-real FP32 and 16-bit links; the FP32
     // 12-real rebuild spills too much under it
     if constexpr (sizeof(typename SOut::real) == 4 && R == 1 && !std::is_same<Lk, LkF32_12>::value)
-        hop_kernel_occ<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
+        hop_kernel_occ<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(q);
     else
-        hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(p);
+        hop_kernel<SIn, SOut, SX, Lk, Dag, Axpy, R><<<grid, threads, 0, s>>>(q);
     WEO_CUDA(cudaGetLastError());
     return WEO_OK;
 }

@@ -174,3 +174,7 @@ def test_tile_links_rejects_null(lib):
 
 def test_l2_peak_rejects_null(lib):
     assert lib.wilson_eo_l2_peak(None, None) == -1
+
+
+def test_site_blocks_rejects_null_and_bad_values(lib):
+    assert lib.wilson_eo_set_site_blocks(None, 1) == -1

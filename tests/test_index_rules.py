@@ -607,3 +607,34 @@ def test_fused_staged_round_robin_always_progresses(grid, lt, lookahead):
             remaining -= 1
             moved = True
         assert moved, "no CTA can progress"
+
+
+def blocked_site_of(dims, b, t):
+    """The hop kernels' blocked site order (CTA b, thread t): rows
+    (y0 + dy, z0 + dz, t0 + dt) of 2x2x2 blocks, Lx/2 threads per row."""
+    lx, ly, lz, lt = dims
+    lxh = lx // 2
+    hy, hz = ly // 2, lz // 2
+    y0, z0, t0 = 2 * (b % hy), 2 * ((b // hy) % hz), 2 * (b // (hy * hz))
+    row, xh = divmod(t, lxh)
+    return (((t0 + (row >> 2)) * lz + z0 + ((row >> 1) & 1)) * ly + y0 + (row & 1)) * lxh + xh
+
+
+@pytest.mark.parametrize("dims", [(16, 2, 2, 2), (16, 4, 6, 8), (32, 8, 4, 2), (24, 6, 2, 4), (64, 2, 4, 2)])
+def test_blocked_site_order_is_a_permutation(dims):
+    """Every site exactly once over the (Ly/2)(Lz/2)(Lt/2) CTAs of 8 Lx/2 threads,
+    and each CTA's sites are 8 whole rows forming a 2x2x2 block in (y, z, t)."""
+    lx, ly, lz, lt = dims
+    lxh, vh = lx // 2, lx * ly * lz * lt // 2
+    nb = (ly // 2) * (lz // 2) * (lt // 2)
+    seen = []
+    for b in range(nb):
+        sites = [blocked_site_of(dims, b, t) for t in range(8 * lxh)]
+        rows = sorted({s // lxh for s in sites})
+        assert len(rows) == 8 and all(len([s for s in sites if s // lxh == r]) == lxh for r in rows)
+        ys = {r % ly for r in rows}
+        zs = {(r // ly) % lz for r in rows}
+        ts = {r // (ly * lz) for r in rows}
+        assert len(ys) == len(zs) == len(ts) == 2
+        seen += sites
+    assert sorted(seen) == list(range(vh))
