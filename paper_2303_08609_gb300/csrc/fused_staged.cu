@@ -27,7 +27,8 @@
 // at even sites) plus eZ of the tile in plane z-1 and eT of the tile in plane
 // t-1; B copies oX .. oYh plus oZ of tile (z-1) and oT of tile (t-1). Both hops
 // read the same block bytes, so with B running a few slices after A the
-// second read of a link comes from L2, and a link leaves HBM once per M_eo.
+// second read of a link comes from L2, and a link leaves HBM about once per
+// M_eo.
 // The blocks take 576 T + 144 Lx/2 bytes per tile: the packed field plus the
 // halo rows (+6 % at 32^3 x 64).
 //
@@ -216,7 +217,8 @@ __device__ __forceinline__ int fs_row(const FsParams &P, int z, int t, int y)
 
 // issue the copies of item `it` into the stage at `base`
 // pol_a: link copies of first-hop items (read again by the second hop of the
-// same slices: kept in L2); pol_b: those of second-hop items (last use)
+// same slices: normal L2 priority); pol_b: those of second-hop items (last
+// use: evict first)
 __device__ __forceinline__ void fs_issue(const FsParams &P, const FsItem &it, char *base, uint64_t *full,
                                          uint64_t pol_a, uint64_t pol_b)
 {
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(32 * (2 * NS * 2 + 1), 1) fused_staged_kernel(
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.in_row)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mid_tile)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.mid_row)) : "memory");
-        const uint64_t pol_a = policy_evict_last(), pol_b = policy_evict_first();
+        const uint64_t pol_a = policy_evict_normal(), pol_b = policy_evict_first();
         const unsigned need = (unsigned)(P.tps * P.tpt);  // team stores of one slice
         int known[4] = {-1, -1, -1, -1};  // slices seen complete (most recent four)
         int kn = 0;

@@ -55,11 +55,12 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// L2 policy for data read again soon by another item (kept over evict-first data)
-__device__ __forceinline__ uint64_t policy_evict_last()
+// L2 policy for data read again soon by another item (normal priority, above
+// the evict-first streams)
+__device__ __forceinline__ uint64_t policy_evict_normal()
 {
     uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 
