@@ -464,7 +464,11 @@ def run_ours(args, rank, world, local):
 
     # ---- other storage formats (same workload, M_eo^dag M_eo per step)
     variants = {}
-    if not args.no_variants:
+    # the side measurements (other formats, multi-RHS, batches, force, solves and
+    # their oracle checks) run in single-GPU runs only: a replica run measures
+    # the main step and the end-to-end step on every rank
+    side = world == 1
+    if not args.no_variants and side:
         Ud = torch.from_numpy(U).to(dev)
         # algo 0: two hop launches, 1: fused, 2: two staged (TMA) hop launches,
         # 3: fused staged (one TMA-fed launch)
@@ -578,10 +582,10 @@ def run_ours(args, rank, world, local):
         del xv, yv, zv
         del Ud
 
-    extra = {} if args.no_extras else extras(U, psi, dev, stream)
-    if not args.no_solve:
+    extra = {} if args.no_extras or not side else extras(U, psi, dev, stream)
+    if not args.no_solve and side:
         extra["multi_rhs_solve_12"] = multi_solve_comparison(U, dev)
-    solve = None if args.no_solve else solve_comparison(dev, tuple(args.solve_dims),
+    solve = None if args.no_solve or not side else solve_comparison(dev, tuple(args.solve_dims),
                                                         args.solve_variants)
 
     cpu = None
