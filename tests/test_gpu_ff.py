@@ -97,9 +97,12 @@ def test_mixed_solve_with_ff_residuals(weo, oracle_lib, prec):
         assert np.linalg.norm(b - ax) / np.linalg.norm(b) <= 1.5e-10
         res[mode] = info
         op.close()
+    # a zero initial guess starts from r = b with no operator application; every
+    # reliable update then forms one true residual (float-float in mode 1, with
+    # at most a native FP64 confirmation of convergence; native FP64 in mode 0)
     assert res[1]["ff_applies"] >= res[1]["reliable_updates"]
     assert res[1]["fp64_applies"] <= 2 and res[0]["ff_applies"] == 0
-    assert res[0]["fp64_applies"] == res[0]["reliable_updates"] + 1
+    assert res[0]["fp64_applies"] == res[0]["reliable_updates"]
     assert abs(res[1]["iterations"] - res[0]["iterations"]) <= 16
 
 
