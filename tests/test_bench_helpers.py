@@ -57,3 +57,17 @@ def test_traffic_entries_name_their_sources():
     assert "hop_staged.cu" in bench.sources_for("hop_staged_f32_l18_axpy")
     assert "fused.cu" in bench.sources_for("fused_f32_l18_axpy")
     assert "hop_staged.cu" not in bench.sources_for("hop_f32_l18")
+
+
+def test_both_arms_report_the_same_workload_config():
+    """The reference arm and our arm print the same `config` dict (the workload,
+    not the implementation: that goes to `impl_config` / `sample_lattice`)."""
+    import argparse
+
+    ns = argparse.Namespace(prec="f32", linkfmt=18, ff=False)
+    cfg = bench.workload_config(ns, 1)
+    assert set(cfg) == {"workload", "lattice", "kappa", "links", "prec", "flop_per_site_per_meo", "l2",
+                        "parallelism"}
+    assert cfg["lattice"] == [32, 32, 32, 64] and cfg["flop_per_site_per_meo"] == 1344
+    assert "32x32x32x64" in cfg["workload"] and "FP32" in cfg["workload"]
+    assert bench.workload_config(ns, 4)["parallelism"] == "replicas"
