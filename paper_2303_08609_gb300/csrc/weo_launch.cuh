@@ -2,6 +2,7 @@
 // compile-time instance. Included by one translation unit per precision.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 
 #include "weo_internal.h"
@@ -25,12 +26,13 @@ int launch_tile_links(const HopParams &p, cudaStream_t s)
     constexpr int T = 256 / NRL;
     const size_t smem = (size_t)576 * T;
     auto kern = hop_kernel_tile_links<SIn, SOut, SX, Lk, Dag, Axpy, NRL, RP>;
-    if (smem > 48 * 1024) {
-        static bool attr_set = false;  // per instance; idempotent if two threads race
-        if (!attr_set) {
-            WEO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr_set = true;
-        }
+    if (smem > 48 * 1024) {  // opt in to more than 48 KB, once per instance
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        std::call_once(once, [&] {
+            attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        WEO_CUDA(attr);
     }
     kern<<<(unsigned)((p.vh + T - 1) / T), 256, smem, s>>>(p);
     WEO_CUDA(cudaGetLastError());
